@@ -1,0 +1,206 @@
+/*
+ * vasmg.h -- C ABI of the GB300 (sm_103a) V-ASMG-preconditioned CG library.
+ *
+ * The library solves A U = F (Sec. 1, eq. (equ)) where A is the stiffness
+ * matrix of P1 (linear Lagrange) finite elements for isotropic linear
+ * elasticity in 2D or 3D (Sec. 2, eq. (prob) and the block form of A), with
+ * PCG (Alg. 2) preconditioned by one V-cycle (Alg. 3, applied recursively) of
+ * the vertex-based auxiliary space multigrid of Sec. 3: a region quadtree /
+ * octree over the mesh vertices (Sec. 3.1.1), coarser grids by merging the
+ * deepest cells (Sec. 3.1.2), bilinear / trilinear transfers (Sec. 3.2,
+ * eq. (wkl)), Galerkin coarse operators (eq. (R), (Ac)), multicolour block
+ * Gauss-Seidel smoothing (Sec. 2.1, Alg. 1) and a direct solve on the
+ * coarsest grid (Sec. 3, Step 2.3).
+ *
+ * Conventions
+ *  - Every function returns VASMG_OK (0) on success, VASMG_NOT_CONVERGED (+1)
+ *    when PCG hit max_iters (U then holds the last iterate), or a negative
+ *    VASMG_ERR_* code.  No C++ exception crosses this boundary.
+ *  - Degree of freedom numbering is vertex-interleaved: dof = vertex*dim + c.
+ *  - Problem arrays are host memory owned by the caller; vasmg_setup copies
+ *    them and keeps nothing that points into them.  The handle owns all device
+ *    memory of one hierarchy until vasmg_destroy.
+ *  - Vector arguments (F, U, x, y) may be host or device pointers (copies use
+ *    unified addressing, cudaMemcpyDefault).  They are FP64 arrays of length
+ *    n = dim * n_vertices unless stated otherwise.
+ *  - All device work of a handle runs on options.stream (NULL = the legacy
+ *    default stream).  One thread may use a handle at a time.
+ *  - A device wait inside a kernel that gives up returns VASMG_ERR_TIMEOUT;
+ *    the context stays usable.
+ */
+#ifndef VASMG_H
+#define VASMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  VASMG_OK = 0,
+  VASMG_NOT_CONVERGED = 1,
+  VASMG_ERR_INVALID_ARG = -1,
+  VASMG_ERR_DEGENERATE_ELEMENT = -2, /* an element has zero (or non-finite) measure */
+  VASMG_ERR_OOM = -3,
+  VASMG_ERR_CUDA = -4,
+  VASMG_ERR_BREAKDOWN = -5,          /* p^T q <= 0 or NaN inside PCG */
+  VASMG_ERR_TIMEOUT = -6,            /* a bounded device wait gave up */
+  VASMG_ERR_UNSUPPORTED = -7
+};
+
+/* Precision of the V-cycle.  The outer CG (SpMV, dot products, updates) and
+ * the coarsest factorisation are always FP64. */
+enum {
+  VASMG_FP64 = 0,                    /* V-cycle in FP64 storage and arithmetic */
+  VASMG_FP32_VCYCLE = 1,             /* operators, transfers, vectors FP32 */
+  VASMG_FP32_VCYCLE_BF16_SMOOTH = 2  /* as FP32, with operator values stored BF16 */
+};
+
+typedef struct vasmg_ctx* vasmg_handle;
+
+/* The problem statement of Sec. 2: vertices, P1 simplices, Lame parameters
+ * (mu = E/(2(1+nu)), lambda = E nu/((1+nu)(1-2nu))) and Dirichlet data. */
+typedef struct {
+  int32_t dim;                 /* 2 or 3 */
+  int64_t n_vertices;
+  const double* coords;        /* [n_vertices*dim], vertex-major */
+  int64_t n_elements;
+  const int32_t* elements;     /* [n_elements*(dim+1)], 0-based vertex ids */
+  const double* lambda;        /* [n_elements] or NULL -> lambda_const */
+  const double* mu;            /* [n_elements] or NULL -> mu_const */
+  double lambda_const, mu_const;
+  int64_t n_dirichlet;
+  const int64_t* dirichlet_dofs;   /* [n_dirichlet], dof = vertex*dim + component */
+  const double* dirichlet_values;  /* [n_dirichlet] or NULL -> homogeneous */
+} vasmg_problem;
+
+typedef struct {
+  int32_t leaf_threshold;      /* a region-tree cell splits when it holds more
+                                  vertices than this (Sec. 3.1.1 Step 2: 4 in
+                                  2D); default 4 in 2D, 8 in 3D */
+  int32_t n_pre, n_post;       /* smoothing sweeps; only 1, 1 is supported */
+  int32_t precision;           /* VASMG_FP64 | VASMG_FP32_VCYCLE | ..._BF16_SMOOTH */
+  int64_t coarse_max_dofs;     /* 0: coarsen to the root cell (Sec. 3.1.2);
+                                  else stop at the first level with at most this
+                                  many dofs (<= 4096) */
+  int32_t max_iters;           /* PCG iteration cap, default 1000 */
+  int32_t use_graph;           /* 1: one CUDA graph per solve (device-side loop) */
+  void* stream;                /* cudaStream_t used for all device work */
+} vasmg_options;
+
+typedef struct {
+  int32_t iterations;          /* number of products A p (Alg. 2) */
+  double rel_res;              /* ||r_k|| / ||F|| of the recursive residual */
+  double setup_ms, solve_ms;   /* wall-clock of vasmg_setup / vasmg_solve */
+  int32_t n_levels;            /* fine level + coarse levels */
+  double op_complexity;        /* sum_l nnzb_l / nnzb_0 */
+  double* res_history;         /* caller-owned host array or NULL */
+  int32_t res_history_cap;
+} vasmg_stats;
+
+/* Fill *out with the defaults for dim (2 or 3). */
+int vasmg_default_options(int dim, vasmg_options* out);
+
+/* Assemble A (Sec. 2), impose Dirichlet rows, build the region tree, the
+ * coarse grids, transfers and Galerkin operators (Sec. 3), colour every level,
+ * and factor the coarsest operator -- all on the device.  Returns
+ * VASMG_ERR_DEGENERATE_ELEMENT if an element has zero measure,
+ * VASMG_ERR_INVALID_ARG for out-of-range ids or sizes. */
+int vasmg_setup(const vasmg_problem* problem, const vasmg_options* options, vasmg_handle* out);
+
+/* F = consistent load of a constant body force f (Sec. 2, F_1, F_2):
+ * F_i += f |K| / (dim+1) over the elements K containing vertex i.
+ * body_force: host [dim].  F: host or device [n]. */
+int vasmg_assemble_load(vasmg_handle h, const double* body_force, double* F);
+
+/* PCG (Alg. 2) with the V-ASMG V-cycle as preconditioner, U0 = 0, until
+ * ||F - A U|| / ||F|| < tol (Sec. 5, item (3)).  F: [n], entries at Dirichlet
+ * dofs are ignored; U: [n] output, Dirichlet values written in.  st may be
+ * NULL.  Returns VASMG_OK, VASMG_NOT_CONVERGED or an error. */
+int vasmg_solve(vasmg_handle h, const double* F, double* U, double tol, vasmg_stats* st);
+
+/* Solve k independent systems (uneven sizes allowed), each to tol, sharing
+ * the device; h[i] may repeat.  st may be NULL or an array of k stats. */
+int vasmg_solve_batch(int32_t k, const vasmg_handle* h, const double* const* F, double* const* U, double tol,
+                      vasmg_stats* st);
+
+/* Number of levels (fine + coarse). */
+int vasmg_num_levels(vasmg_handle h);
+
+/* Vertices, off-diagonal-inclusive block count and colour count of a level. */
+int vasmg_level_info(vasmg_handle h, int32_t level, int64_t* n_vertices, int64_t* nnzb, int32_t* n_colours);
+
+/* Export selectors for vasmg_export (all in canonical order: level 0 =
+ * input vertex ids, level >= 1 = ascending lattice key). */
+enum {
+  VASMG_EXPORT_MORTON = 0,       /* u64[n_vertices] Morton keys of the quantised coordinates */
+  VASMG_EXPORT_LEAF = 1,         /* i64[2*n_vertices] (depth, cell key) of each vertex's leaf */
+  VASMG_EXPORT_CELLS = 3,        /* i64[2*ncells] (depth, cell key) of the cells of a level >= 1 */
+  VASMG_EXPORT_LATTICE = 4,      /* u64[nv_l] lattice-corner keys of a level >= 1 */
+  VASMG_EXPORT_P_RP = 5,         /* i64[nv_l+1] interpolation rows (level l -> l+1) */
+  VASMG_EXPORT_P_CI = 6,         /* i32[nnz] */
+  VASMG_EXPORT_P_W = 7,          /* f64[nnz] */
+  VASMG_EXPORT_A_RP = 8,         /* i64[nv_l+1] operator block pattern (with diagonal) */
+  VASMG_EXPORT_A_CI = 9,         /* i32[nnzb] */
+  VASMG_EXPORT_A_V = 10,         /* f64[nnzb*dim*dim] row-major blocks (FP64 values) */
+  VASMG_EXPORT_DEAD = 11,        /* u8[nv_l*dim] 1 = dof removed (Dirichlet / empty column) */
+  VASMG_EXPORT_COLOUR = 12,      /* i32[nv_l] */
+  VASMG_EXPORT_DINV = 13,        /* f64[nv_l*dim*dim] inverses of the diagonal blocks */
+  VASMG_EXPORT_BOX = 14,         /* f64[2] bounding square (m, M) */
+  VASMG_EXPORT_LIFT = 15,        /* f64[n] A u_D of the Dirichlet data */
+  VASMG_EXPORT_VOL = 16          /* f64[n_elements] element measures */
+};
+
+/* Copy an exported array to host buffer buf (NULL: only report the size).
+ * *bytes receives the byte count. */
+int vasmg_export(vasmg_handle h, int32_t what, int32_t level, void* buf, int64_t* bytes);
+
+/* Single steps of the hot path, for parity testing: all vectors FP64 in
+ * canonical order, device or host pointers.
+ *   VASMG_OP_MATVEC      y = A_l x (level 0: the FP64 operator of the outer CG;
+ *                        level > 0: the V-cycle operator, in its precision)
+ *   VASMG_OP_SMOOTH_FWD  y = one forward multicolour sweep from x = 0 on A_l y = x
+ *   VASMG_OP_SMOOTH_BWD  y = one backward sweep on A_l y = x from y's input value
+ *   VASMG_OP_RESIDUAL    y = r after a zero-start forward sweep on A_l z = x
+ *   VASMG_OP_RESTRICT    y = R x (level l -> l+1, y has nv_{l+1}*dim entries)
+ *   VASMG_OP_PROLONG     y += P x (level l+1 -> l, x has nv_{l+1}*dim entries)
+ *   VASMG_OP_COARSE      y = A_L^{-1} x on the coarsest level (Cholesky)
+ *   VASMG_OP_VCYCLE      y = M x, one V-cycle from level l down */
+enum {
+  VASMG_OP_MATVEC = 0,
+  VASMG_OP_SMOOTH_FWD = 1,
+  VASMG_OP_SMOOTH_BWD = 2,
+  VASMG_OP_RESIDUAL = 3,
+  VASMG_OP_RESTRICT = 4,
+  VASMG_OP_PROLONG = 5,
+  VASMG_OP_COARSE = 6,
+  VASMG_OP_VCYCLE = 7
+};
+int vasmg_apply(vasmg_handle h, int32_t op, int32_t level, const double* x, double* y);
+
+/* Timing helper: launch kernel class `which` (VASMG_KERNEL_*) `reps` times on
+ * the handle's stream between two CUDA events; *ms = mean per launch and
+ * *bytes = algorithmic bytes that one launch moves. */
+enum {
+  VASMG_KERNEL_SPMV64 = 0,       /* level-0 FP64 SpMV with fused p.q */
+  VASMG_KERNEL_SWEEP = 1,        /* one full multicolour sweep of level `level` */
+  VASMG_KERNEL_VCYCLE = 2        /* one V-cycle from level 0 */
+};
+int vasmg_time_kernel(vasmg_handle h, int32_t which, int32_t level, int32_t reps, double* ms, double* bytes);
+
+/* Kernels launched by the last vasmg_solve (for accounting). */
+int64_t vasmg_last_launch_count(vasmg_handle h);
+
+int vasmg_destroy(vasmg_handle h);
+
+const char* vasmg_error_string(int code);
+
+/* Human-readable detail of the last error raised on the calling thread. */
+const char* vasmg_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VASMG_H */

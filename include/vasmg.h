@@ -183,9 +183,11 @@ int vasmg_apply(vasmg_handle h, int32_t op, int32_t level, const double* x, doub
  * the handle's stream between two CUDA events; *ms = mean per launch and
  * *bytes = algorithmic bytes that one launch moves. */
 enum {
-  VASMG_KERNEL_SPMV64 = 0,       /* level-0 FP64 SpMV with fused p.q */
-  VASMG_KERNEL_SWEEP = 1,        /* one full multicolour sweep of level `level` */
-  VASMG_KERNEL_VCYCLE = 2        /* one V-cycle from level 0 */
+  VASMG_KERNEL_SPMV64 = 0,       /* level-0 FP64 SpMV (SELL-32) */
+  VASMG_KERNEL_SWEEP = 1,        /* one backward multicolour sweep of level `level` */
+  VASMG_KERNEL_VCYCLE = 2,       /* one V-cycle from level 0 */
+  VASMG_KERNEL_DOWN = 3,         /* pre-smooth + residual + restriction of level `level` */
+  VASMG_KERNEL_UP = 4            /* prolongation + post-smooth of level `level` */
 };
 int vasmg_time_kernel(vasmg_handle h, int32_t which, int32_t level, int32_t reps, double* ms, double* bytes);
 

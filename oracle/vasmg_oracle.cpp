@@ -653,15 +653,37 @@ void galerkin(const Oracle& o, const Level& fine, Level& coarse) {
 
 // ---------------------------------------------------------------- colouring
 
-// Greedy colouring in decreasing priority splitmix64(vertex): each vertex takes
-// the smallest colour unused by its already-coloured neighbours.  (Jones-
-// Plassmann with the same priorities yields exactly this colouring.)
-void colour_level(Level& lv) {
+// Colouring priority.  Fine level: splitmix64(vertex).  Coarser levels (the
+// vertices are lattice points): lattice class first, then splitmix64 -- the
+// class of a vertex is sum_a ((p_a / u) mod 3) 3^a with u the side of the
+// level's smallest cell, and class 0 ranks highest.  On a uniform level the
+// Galerkin stencil has radius 2 cells, so vertices of one class are never
+// neighbours and the greedy colouring uses 3^d colours there.
+u64 colour_priority(const Oracle& o, const Level& lv, size_t l, i64 v) {
+  if (l == 0) return splitmix64((u64)v);
+  int D = 0;
+  for (auto& c : lv.cells) D = std::max(D, c.depth);
+  const int sh = o.K - D;
+  u64 p[3];
+  deinterleave(lv.lat[v], o.dim, o.K + 1, p);
+  u64 cls = 0, w = 1;
+  for (int a = 0; a < o.dim; ++a) {
+    cls += ((p[a] >> sh) % 3) * w;
+    w *= 3;
+  }
+  const u64 ncls = w;  // 9 or 27
+  return ((ncls - 1 - cls) << 58) | (splitmix64((u64)v) >> 6);
+}
+
+// Greedy colouring in decreasing priority (ties: smaller vertex first): each
+// vertex takes the smallest colour unused by its already-coloured neighbours.
+// (Jones-Plassmann with the same priorities yields exactly this colouring.)
+void colour_level(const Oracle& o, Level& lv, size_t l) {
   const BSR& A = lv.A;
   std::vector<std::pair<u64, int32_t>> order;
-  for (i64 v = 0; v < lv.nv; ++v) order.push_back({splitmix64((u64)v), (int32_t)v});
+  for (i64 v = 0; v < lv.nv; ++v) order.push_back({colour_priority(o, lv, l, v), (int32_t)v});
   std::sort(order.begin(), order.end(), [](const std::pair<u64, int32_t>& a, const std::pair<u64, int32_t>& b) {
-    return a.first > b.first;
+    return a.first != b.first ? a.first > b.first : a.second < b.second;
   });
   lv.colour.assign(lv.nv, -1);
   lv.ncol = 0;
@@ -827,7 +849,7 @@ int setup(Oracle& o, const i64* order) {
   L0.A = std::move(A);
   L0.dead.assign(o.is_dir.begin(), o.is_dir.end());
   if (o.coarse_max_dofs > 0 && o.nv * d <= o.coarse_max_dofs) {
-    colour_level(o.L[0]);
+    colour_level(o, o.L[0], 0);
     diag_inverses(o, o.L[0]);
     factor_coarsest(o);
     return 0;
@@ -854,9 +876,9 @@ int setup(Oracle& o, const i64* order) {
     build_Pl(o, f, o.L.back());
     galerkin(o, f, o.L.back());
   }
-  for (auto& lv : o.L) {
-    colour_level(lv);
-    diag_inverses(o, lv);
+  for (size_t l = 0; l < o.L.size(); ++l) {
+    colour_level(o, o.L[l], l);
+    diag_inverses(o, o.L[l]);
   }
   factor_coarsest(o);
   return 0;

@@ -3,12 +3,16 @@
 // inverses, transfers), plus the dense Cholesky factor of the coarsest level.
 //
 // Colouring (the smoother of Sec. 2.1 / Alg. 1 run as multicolour point-block
-// Gauss-Seidel): Jones-Plassmann rounds with priority splitmix64(vertex); a
-// vertex whose uncoloured neighbours all have lower priority takes the
-// smallest colour unused by its coloured neighbours.  Every vertex is coloured
-// after all its higher-priority neighbours and before any lower-priority one,
-// so the result equals greedy colouring in decreasing priority order and does
-// not depend on execution order.
+// Gauss-Seidel): Jones-Plassmann rounds; a vertex whose uncoloured neighbours
+// all rank lower takes the smallest colour unused by its coloured neighbours.
+// Every vertex is coloured after all its higher-ranked neighbours and before
+// any lower-ranked one, so the result equals greedy colouring in rank order
+// and does not depend on execution order.
+// Rank: on the fine level splitmix64(vertex); on coarser levels (lattice
+// points) the class sum_a ((p_a / u) mod 3) 3^a first, class 0 highest, with u
+// the side of the level's smallest cell, then splitmix64(vertex) >> 6; ties go
+// to the smaller vertex.  Uniform coarse levels (radius-2 stencils) then need
+// exactly 3^d colours.
 #include <algorithm>
 
 #include "common.cuh"
@@ -17,16 +21,29 @@ namespace vasmg {
 
 constexpr int MAX_COLOURS = 512;
 
+__device__ __forceinline__ u64 colour_rank(i64 v, const u64* __restrict__ lat, int sh, int d) {
+  if (lat == nullptr) return splitmix64((u64)v);
+  u64 p[3] = {0, 0, 0};
+  unmorton(lat[v], d, p);
+  u64 cls = 0, w = 1;
+  for (int a = 0; a < d; ++a) {
+    cls += ((p[a] >> sh) % 3ull) * w;
+    w *= 3;
+  }
+  return ((w - 1 - cls) << 58) | (splitmix64((u64)v) >> 6);
+}
+
 __global__ void jp_round_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, i64 nv,
-                                const int32_t* __restrict__ cin, int32_t* __restrict__ cout,
-                                unsigned long long* __restrict__ remaining, int* __restrict__ overflow) {
+                                const u64* __restrict__ lat, int sh, int d, const int32_t* __restrict__ cin,
+                                int32_t* __restrict__ cout, unsigned long long* __restrict__ remaining,
+                                int* __restrict__ overflow) {
   for (i64 v = (i64)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (i64)gridDim.x * blockDim.x) {
     const int32_t cv = cin[v];
     if (cv >= 0) {
       cout[v] = cv;
       continue;
     }
-    const u64 pv = splitmix64((u64)v);
+    const u64 pv = colour_rank(v, lat, sh, d);
     u64 used[MAX_COLOURS / 64];
 #pragma unroll
     for (int w = 0; w < MAX_COLOURS / 64; ++w) used[w] = 0;
@@ -36,7 +53,8 @@ __global__ void jp_round_kernel(const int32_t* __restrict__ rp, const int32_t* _
       if (j == (int32_t)v) continue;
       const int32_t cj = cin[j];
       if (cj < 0) {
-        if (splitmix64((u64)j) > pv) {
+        const u64 pj = colour_rank(j, lat, sh, d);
+        if (pj > pv || (pj == pv && j < (int32_t)v)) {
           eligible = false;
           break;
         }
@@ -62,7 +80,7 @@ __global__ void jp_round_kernel(const int32_t* __restrict__ rp, const int32_t* _
   }
 }
 
-static int colour_level(Ctx& c, CanonLevel& lv) {
+static int colour_level(Ctx& c, CanonLevel& lv, int l) {
   cudaStream_t s = c.stream;
   DevBuf<int32_t> a, b;
   a.alloc(lv.nv, s);
@@ -75,8 +93,9 @@ static int colour_level(Ctx& c, CanonLevel& lv) {
   ovf.zero();
   for (i64 round = 0; round <= lv.nv; ++round) {
     rem.zero();
-    jp_round_kernel<<<grid_for(lv.nv, 256), 256, 0, s>>>(lv.rp.get(), lv.ci.get(), lv.nv, a.get(), b.get(), rem.get(),
-                                                          ovf.get());
+    jp_round_kernel<<<grid_for(lv.nv, 256), 256, 0, s>>>(lv.rp.get(), lv.ci.get(), lv.nv,
+                                                          l == 0 ? nullptr : lv.lat.get(), c.K - lv.max_depth,
+                                                          c.dim, a.get(), b.get(), rem.get(), ovf.get());
     check_launch("jp_round");
     std::swap(a, b);
     if (fetch(rem.get(), s) == 0) break;
@@ -357,7 +376,7 @@ void setup_colour_and_solve_levels(Ctx& c) {
     CanonLevel& cl = c.C[l];
     SolveLevel& sl = c.S[l];
     sl.nv = cl.nv;
-    cl.ncol = colour_level(c, cl);
+    cl.ncol = colour_level(c, cl, l);
     sl.ncol = cl.ncol;
     // renumber colour by colour (Morton order inside a colour)
     {

@@ -2,53 +2,69 @@
 // (Alg. 3, recursive) of V-ASMG.
 //
 // Outer CG, FP64, level-0 solve order:
-//   spmv_dot     q = A p (diagonal + off-diagonal planes), p.q, alpha = rho / p.q
+//   spmv_sell    q = A p with A in SELL-32 (slices of 32 rows, one thread per
+//                row, diagonal block included), p.q, alpha = rho / p.q.  GB300
+//                runs FP64 at a small fraction of its FP32 rate, so the layout
+//                keeps every lane's DFMA useful;
 //   cg_update    U += alpha p, r -= alpha q, ||r||, stop test ||r||/||F|| < tol
-//                (Sec. 5 item (3)), b_0 = r cast to the V-cycle precision
-//   rz_dot       rho_new = r.z, beta = rho_new / rho
-//   p_update     p = z + beta p
-// Reductions are deterministic: every block writes one partial, and the last
+//                (Sec. 5 item (3)), b_0 = r cast to the V-cycle precision;
+//   rz           rho_new = r.z, beta = rho_new / rho;   p_update  p = z + beta p.
+// Reductions are deterministic: every block writes one partial and the last
 // block to finish sums the partials in index order.
 //
-// V-cycle, level by level (precision V, values stored as S):
-//   pre-smooth   one forward multicolour block Gauss-Seidel sweep from a zero
-//                initial guess: x_i = D_ii^{-1} (b_i - sum_{j of an earlier
-//                colour} A_ij x_j) -- with a zero start the later colours
-//                contribute nothing, so only the "lower" part of each row
-//                (columns of earlier colours come first) is read;
-//   residual     r_i = - sum_{j of a later colour} A_ij x_j: after that sweep
-//                b_i - A_ii x_i - sum_lower A_ij x_j is exactly zero, so only the
-//                "upper" part is read (pre-smooth + residual = one pass over A);
-//   restrict     b_{l+1} = R r_l with R = P^T (eq. (R)), gathered row-wise;
-//   coarsest     A_L e = b by the FP64 Cholesky factor (Sec. 3, Step 2.3);
-//   prolong      x_l += P e_{l+1} (masked at dead dofs);
-//   post-smooth  one backward sweep (colours in reverse order) with full rows.
-// Levels with at most TAIL_NV vertices run in a single one-CTA kernel.
+// V-cycle (precision V, operator values stored as S), for each level that is
+// not small enough for the tail, two self-scheduling launches:
+//   down  forward multicolour block Gauss-Seidel sweep from a zero initial
+//         guess, x_i = D_ii^{-1}(b_i - sum_{j of an earlier colour} A_ij x_j)
+//         (with a zero start the later colours contribute nothing, so only the
+//         "lower" part of each row is read); then the residual
+//         r_i = - sum_{j of a later colour} A_ij x_j (b_i - A_ii x_i - lower is
+//         exactly zero after the sweep); then the restriction b_{l+1} = P^T r
+//         (eq. (R)).  Pre-smoothing + residual read each block once.
+//   up    prolongation x_l += P x_{l+1} (masked at dead dofs), then one backward
+//         sweep (colours in reverse order) with full rows.
+// A launch is a pool of tiles (rows of one colour, residual rows, coarse rows)
+// claimed in order from an atomic counter.  A sweep tile waits only for the
+// tiles of earlier colours that hold its neighbours (per-tile flags stamped
+// with a launch epoch), so colours overlap and no launch or global barrier
+// separates them.  Every wait is bounded; a wait that gives up raises a
+// global abort flag and the solve returns VASMG_ERR_TIMEOUT.  The last block
+// to leave a launch resets its counters and advances the epoch.
 //
-// Every loop of the solve is captured in one CUDA graph with a conditional
-// WHILE node, so a solve is one graph launch (no host round trip per
-// iteration); without graph support the host launches the per-iteration body
-// and reads the stop flag.
+// Levels with at most TAIL_NV vertices and the coarsest Cholesky solve run in
+// one thread-block-cluster kernel (hardware cluster barriers between phases).
+//
+// The whole solve is one CUDA graph with a conditional WHILE node (no host
+// round trip per iteration).
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
 namespace vasmg {
 
-constexpr int TAIL_NV = 4096;
+constexpr int TAIL_NV = 20000;
 constexpr int TAIL_THREADS = 1024;
 constexpr int TAIL_G = 8;
-constexpr int MAX_LEVELS = 48;
+constexpr int MAX_LEVELS = 40;
 constexpr int CG_THREADS = 256;
+constexpr int DF_THREADS = 256;
+constexpr int RC_ROWS = 256;      // coarse rows per restriction tile
+constexpr int RP_ROWS = 256;      // fine rows per prolongation tile
+constexpr int SPIN_LIMIT = 1 << 20;   // ~0.1-0.5 s of polling before a wait gives up
 
 struct Scalars {
   double rho, pq, alpha, beta, rr, res0, relres, tol;
-  int iter, max_iters, done, status, first, bodies;
+  int iter, max_iters, done, status, first, bodies, abort, pad;
   unsigned int cnt[4];
 };
 
-// ------------------------------------------------------------------ loads
+// per-level launch state: [0] down claim [1] down exit [2] residual tiles done
+// [3] down epoch [4] up claim [5] up exit [6] prolongation tiles done [7] up epoch
+enum { C_DCLAIM = 0, C_DEXIT, C_RESDONE, C_DEPOCH, C_UCLAIM, C_UEXIT, C_PRODONE, C_UEPOCH, C_N };
+
+// ------------------------------------------------------------------ memory helpers
 
 template <typename V, typename S>
 __device__ __forceinline__ V ldv(const S* p);
@@ -61,26 +77,62 @@ __device__ __forceinline__ float ldv<float, __nv_bfloat16>(const __nv_bfloat16* 
   return __bfloat162float(__ldg(p));
 }
 
+// vectors written inside a launch by other CTAs are read from L2 (.cg)
+template <typename V>
+__device__ __forceinline__ V ldx(const V* p) { return __ldcg(p); }
+template <typename V>
+__device__ __forceinline__ void stx(V* p, V v) { __stcg(p, v); }
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_i(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ------------------------------------------------------------------ level view
+
 template <typename V>
 struct LV {
-  int nv;
+  int nv, ncol;
   long long nnz;
   const int* rp;
   const int* ci;
-  const int* sp;
+  const int* sp;          // first entry of a later colour in each row
   const void* off;        // planes [d*d][nnz] of S
   const V* dinv;          // planes [d*d][nv]
   const uint8_t* dead;    // per vertex, bit a = component a removed
   V* x;
   V* b;
   V* r;
+  const int* cs;          // colour starts [ncol+1]
   // transfer to level l+1
+  int nvc;
   const int* prp;
   const int* pci;
   const V* pw;
   const int* rrp;
   const int* rci;
   const V* rw;
+  V* bc;                  // b of level l+1
+  const V* xc;            // x of level l+1
+  // self-scheduling state
+  int T;                  // sweep tiles
+  const int* ts;          // tile row starts [T+1]
+  const int* dlo_rp;      // tiles of earlier colours holding neighbours
+  const int* dlo;
+  const int* dhi_rp;      // tiles of later colours holding neighbours
+  const int* dhi;
+  unsigned* fl_down;
+  unsigned* fl_up;
+  int* ctr;               // C_N counters
 };
 
 template <int D>
@@ -95,8 +147,8 @@ __device__ __forceinline__ float pick(const float (&a)[D], int i) {
 // One row of a sweep / residual by a group of G lanes.
 // MODE 0: x_i = Dinv (b_i - lower part), MODE 1: x_i = Dinv (b_i - all
 // off-diagonal blocks), MODE 2: r_i = -(upper part).
-template <int D, int G, typename V, typename S, int MODE>
-__device__ __forceinline__ void row_pass(const LV<V>& L, int row, bool valid, int lane) {
+template <int D, int G, typename V, typename S, int MODE, typename L_t>
+__device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int lane) {
   int k0 = 0, k1 = 0;
   if (valid) {
     k0 = MODE == 2 ? __ldg(L.sp + row) : __ldg(L.rp + row);
@@ -110,7 +162,7 @@ __device__ __forceinline__ void row_pass(const LV<V>& L, int row, bool valid, in
     const int j = __ldg(L.ci + k);
     V xj[D];
 #pragma unroll
-    for (int bb = 0; bb < D; ++bb) xj[bb] = L.x[(long long)j * D + bb];
+    for (int bb = 0; bb < D; ++bb) xj[bb] = ldx(L.x + (long long)j * D + bb);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -122,66 +174,208 @@ __device__ __forceinline__ void row_pass(const LV<V>& L, int row, bool valid, in
     for (int a = 0; a < D; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o, G);
   if (!valid || lane >= D) return;
   if (MODE == 2) {
-    L.r[(long long)row * D + lane] = -pick<D>(acc, lane);
+    stx(L.r + (long long)row * D + lane, -pick<D>(acc, lane));
   } else {
     V s = V(0);
 #pragma unroll
     for (int bb = 0; bb < D; ++bb)
-      s += __ldg(L.dinv + (long long)(lane * D + bb) * L.nv + row) * (L.b[(long long)row * D + bb] - acc[bb]);
-    L.x[(long long)row * D + lane] = s;
+      s += __ldg((const V*)L.dinv + (long long)(lane * D + bb) * L.nv + row) *
+           (ldx((const V*)L.b + (long long)row * D + bb) - acc[bb]);
+    stx(L.x + (long long)row * D + lane, s);
   }
 }
 
-template <int D, int G, typename V, typename S, int MODE>
-__global__ void __launch_bounds__(256) colour_kernel(LV<V> L, int row0, int row1) {
-  const int gid = (int)((blockIdx.x * blockDim.x + threadIdx.x) / G);
-  const int lane = threadIdx.x & (G - 1);
-  const int row = row0 + gid;
-  row_pass<D, G, V, S, MODE>(L, row, row < row1, lane);
-}
-
-template <int D, typename V>
-__device__ __forceinline__ void restrict_row(const LV<V>& L, const LV<V>& C, int I) {
+template <int D, typename V, typename L_t>
+__device__ __forceinline__ void restrict_row(const L_t& L, int I) {
   V acc[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) acc[a] = V(0);
   for (int t = __ldg(L.rrp + I); t < __ldg(L.rrp + I + 1); ++t) {
     const int i = __ldg(L.rci + t);
-    const V w = __ldg(L.rw + t);
+    const V w = __ldg((const V*)L.rw + t);
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] += w * L.r[(long long)i * D + a];
+    for (int a = 0; a < D; ++a) acc[a] += w * ldx((const V*)L.r + (long long)i * D + a);
   }
 #pragma unroll
-  for (int a = 0; a < D; ++a) C.b[(long long)I * D + a] = acc[a];
+  for (int a = 0; a < D; ++a) stx((V*)L.bc + (long long)I * D + a, acc[a]);
 }
 
-template <int D, typename V>
-__device__ __forceinline__ void prolong_row(const LV<V>& L, const LV<V>& C, int i) {
+template <int D, typename V, typename L_t>
+__device__ __forceinline__ void prolong_row(const L_t& L, int i) {
   V acc[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) acc[a] = V(0);
   for (int t = __ldg(L.prp + i); t < __ldg(L.prp + i + 1); ++t) {
     const int J = __ldg(L.pci + t);
-    const V w = __ldg(L.pw + t);
+    const V w = __ldg((const V*)L.pw + t);
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] += w * C.x[(long long)J * D + a];
+    for (int a = 0; a < D; ++a) acc[a] += w * ldx((const V*)L.xc + (long long)J * D + a);
   }
   const uint8_t dm = __ldg(L.dead + i);
 #pragma unroll
   for (int a = 0; a < D; ++a)
-    if (!((dm >> a) & 1)) L.x[(long long)i * D + a] += acc[a];
+    if (!((dm >> a) & 1)) {
+      V* px = (V*)L.x + (long long)i * D + a;
+      stx(px, ldx((const V*)px) + acc[a]);
+    }
 }
 
-template <int D, typename V>
-__global__ void __launch_bounds__(256) restrict_kernel(LV<V> L, LV<V> C) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I < C.nv) restrict_row<D, V>(L, C, I);
+// ------------------------------------------------------------------ self-scheduling helpers
+
+// Wait until every tile in list[0..n) carries `epoch` (warp 0 polls); returns
+// false (uniformly) if a wait gave up or the abort flag is up.
+__device__ __forceinline__ bool wait_tiles(const int* __restrict__ list, int n, const unsigned* flags,
+                                           unsigned epoch, int* abort_flag) {
+  __shared__ int s_ok;
+  if (threadIdx.x < 32) {
+    bool ok = true;
+    for (int k = threadIdx.x; k < n && ok; k += 32) {
+      const unsigned* f = flags + __ldg(list + k);
+      int spins = 0;
+      while (ld_acquire(f) != epoch) {
+        if (++spins > SPIN_LIMIT || *(volatile int*)abort_flag) {
+          atomicExch(abort_flag, 1);
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (threadIdx.x == 0) s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
-template <int D, typename V>
-__global__ void __launch_bounds__(256) prolong_kernel(LV<V> L, LV<V> C) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < L.nv) prolong_row<D, V>(L, C, i);
+__device__ __forceinline__ bool wait_count(const int* ctr, int target, int* abort_flag) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1, spins = 0;
+    while (ld_acquire_i(ctr) < target) {
+      if (++spins > SPIN_LIMIT || *(volatile int*)abort_flag) {
+        atomicExch(abort_flag, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Make this tile's writes visible at GPU scope, then stamp its flag.
+__device__ __forceinline__ void publish_tile(unsigned* flag, unsigned epoch) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(flag, epoch);
+}
+__device__ __forceinline__ void publish_count(int* ctr) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(ctr, 1);
+}
+
+// Claim the next work item; also broadcasts the abort flag.
+__device__ __forceinline__ int claim(int* ctr, const int* abort_flag) {
+  __shared__ int s_t;
+  __syncthreads();
+  if (threadIdx.x == 0) s_t = *(volatile const int*)abort_flag ? INT32_MAX : atomicAdd(ctr, 1);
+  __syncthreads();
+  return s_t;
+}
+
+// The last block to leave resets the launch's counters and advances its epoch.
+__device__ __forceinline__ void leave(int* ctr, int claim_i, int exit_i, int done_i, int epoch_i) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int e = atomicAdd(ctr + exit_i, 1);
+    if (e == (int)gridDim.x - 1) {
+      ctr[claim_i] = 0;
+      ctr[done_i] = 0;
+      ctr[exit_i] = 0;
+      ctr[epoch_i] += 1;
+      __threadfence();
+    }
+  }
+}
+
+// ------------------------------------------------------------------ down / up launches
+
+// phases: 1 forward sweep (zero start), 2 residual, 4 restriction
+template <int D, int G, typename V, typename S>
+__global__ void __launch_bounds__(DF_THREADS) vdown_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
+  __shared__ unsigned s_epoch;
+  if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_DEPOCH);
+  __syncthreads();
+  const unsigned epoch = s_epoch;
+  const int T = L.T;
+  const int nsw = (phases & 1) ? T : 0;
+  const int nres = (phases & 2) ? T : 0;
+  const int nrc = (phases & 4) ? (L.nvc + RC_ROWS - 1) / RC_ROWS : 0;
+  const int total = nsw + nres + nrc;
+  constexpr int NG = DF_THREADS / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  for (;;) {
+    const int t = claim(L.ctr + C_DCLAIM, &sc->abort);
+    if (t >= total) break;
+    if (t < nsw) {
+      const int b0 = __ldg(L.dlo_rp + t), b1 = __ldg(L.dlo_rp + t + 1);
+      if (!wait_tiles(L.dlo + b0, b1 - b0, L.fl_down, epoch, &sc->abort)) break;
+      const int r0 = __ldg(L.ts + t), r1 = __ldg(L.ts + t + 1);
+      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 0>(L, base + g, base + g < r1, lane);
+      publish_tile(L.fl_down + t, epoch);
+    } else if (t < nsw + nres) {
+      const int tt = t - nsw;
+      const int b0 = __ldg(L.dhi_rp + tt), b1 = __ldg(L.dhi_rp + tt + 1);
+      if (!wait_tiles(L.dhi + b0, b1 - b0, L.fl_down, epoch, &sc->abort)) break;
+      const int r0 = __ldg(L.ts + tt), r1 = __ldg(L.ts + tt + 1);
+      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 2>(L, base + g, base + g < r1, lane);
+      publish_count(L.ctr + C_RESDONE);
+    } else {
+      const int tc = t - nsw - nres;
+      if (nres && !wait_count(L.ctr + C_RESDONE, T, &sc->abort)) break;
+      const int I = tc * RC_ROWS + (int)threadIdx.x;
+      if (threadIdx.x < RC_ROWS && I < L.nvc) restrict_row<D, V>(L, I);
+    }
+  }
+  leave(L.ctr, C_DCLAIM, C_DEXIT, C_RESDONE, C_DEPOCH);
+}
+
+// phases: 1 prolongation + correction, 2 backward sweep
+template <int D, int G, typename V, typename S>
+__global__ void __launch_bounds__(DF_THREADS) vup_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
+  __shared__ unsigned s_epoch;
+  if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_UEPOCH);
+  __syncthreads();
+  const unsigned epoch = s_epoch;
+  const int T = L.T;
+  const int npr = (phases & 1) ? (L.nv + RP_ROWS - 1) / RP_ROWS : 0;
+  const int nsw = (phases & 2) ? T : 0;
+  const int total = npr + nsw;
+  constexpr int NG = DF_THREADS / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  for (;;) {
+    const int t = claim(L.ctr + C_UCLAIM, &sc->abort);
+    if (t >= total) break;
+    if (t < npr) {
+      const int i = t * RP_ROWS + (int)threadIdx.x;
+      if (threadIdx.x < RP_ROWS && i < L.nv) prolong_row<D, V>(L, i);
+      publish_count(L.ctr + C_PRODONE);
+    } else {
+      const int tile = T - 1 - (t - npr);  // colours in reverse order
+      if (npr && !wait_count(L.ctr + C_PRODONE, npr, &sc->abort)) break;
+      const int b0 = __ldg(L.dhi_rp + tile), b1 = __ldg(L.dhi_rp + tile + 1);
+      if (!wait_tiles(L.dhi + b0, b1 - b0, L.fl_up, epoch, &sc->abort)) break;
+      const int r0 = __ldg(L.ts + tile), r1 = __ldg(L.ts + tile + 1);
+      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 1>(L, base + g, base + g < r1, lane);
+      publish_tile(L.fl_up + tile, epoch);
+    }
+  }
+  leave(L.ctr, C_UCLAIM, C_UEXIT, C_PRODONE, C_UEPOCH);
 }
 
 // ------------------------------------------------------------------ coarsest solve and tail
@@ -201,7 +395,7 @@ __device__ void coarse_solve_warp(const CoarseArgs& A, const V* b, V* x) {
   const int n = A.n, d = A.d;
   for (int t = lane; t < n; t += 32) {
     const int r = t / d, a = t - r * d;
-    A.y[(long long)__ldg(A.perm + r) * d + a] = (double)b[t];
+    A.y[(long long)__ldg(A.perm + r) * d + a] = (double)ldx(b + t);
   }
   __syncwarp();
   for (int j = 0; j < n; ++j) {
@@ -222,7 +416,7 @@ __device__ void coarse_solve_warp(const CoarseArgs& A, const V* b, V* x) {
   }
   for (int t = lane; t < n; t += 32) {
     const int r = t / d, a = t - r * d;
-    x[t] = (V)A.y[(long long)__ldg(A.perm + r) * d + a];
+    stx(x + t, (V)A.y[(long long)__ldg(A.perm + r) * d + a]);
   }
 }
 
@@ -231,49 +425,88 @@ __global__ void coarse_kernel(CoarseArgs A, const V* b, V* x) {
   if (threadIdx.x < 32) coarse_solve_warp<V>(A, b, x);
 }
 
+// A level as the tail kernel sees it (the fields row_pass and the transfers use).
+template <typename V>
+struct TL {
+  int nv;
+  long long nnz;
+  const int* rp;
+  const int* ci;
+  const int* sp;
+  const void* off;
+  const V* dinv;
+  const uint8_t* dead;
+  V* x;
+  V* b;
+  V* r;
+  const int* cs;
+  int ncol, nvc;
+  const int* prp;
+  const int* pci;
+  const V* pw;
+  const int* rrp;
+  const int* rci;
+  const V* rw;
+  V* bc;
+  const V* xc;
+};
+
 template <typename V>
 struct TailArgs {
   int l0, L;                     // levels l0..L handled here, L = coarsest
-  LV<V> lv[MAX_LEVELS];
-  const int* cs[MAX_LEVELS];     // colour starts per level (device)
-  int ncol[MAX_LEVELS];
+  TL<V> lv[MAX_LEVELS];
   CoarseArgs co;
 };
 
-// The V-cycle of all small levels in one CTA (phases separated by
-// __syncthreads; every group runs the same number of loop trips so the
-// sub-warp shuffles stay converged).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// The V-cycle of all small levels in one cluster of CTAs, phases separated by
+// hardware cluster barriers; every group runs the same number of loop trips
+// so the sub-warp shuffles stay converged.
 template <int D, typename V, typename S>
-__global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs<V>* __restrict__ T) {
+__global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constant__ TailArgs<V> A) {
   constexpr int G = TAIL_G;
-  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1), ng = blockDim.x / G;
-  const int l0 = T->l0, Lc = T->L;
+  const int nct = (int)cluster_size(), rank = (int)cluster_rank();
+  const int ng = blockDim.x / G;
+  const int gg = rank * ng + (int)threadIdx.x / G, NG = nct * ng;
+  const int lane = threadIdx.x & (G - 1);
+  const int tid = rank * blockDim.x + threadIdx.x, NT = nct * blockDim.x;
+  const int l0 = A.l0, Lc = A.L;
   for (int l = l0; l < Lc; ++l) {
-    const LV<V>& L = T->lv[l];
-    const int* cs = T->cs[l];
-    for (int c = 0; c < T->ncol[l]; ++c) {
-      const int r0 = cs[c], r1 = cs[c + 1];
-      for (int base = r0; base < r1; base += ng) row_pass<D, G, V, S, 0>(L, base + g, base + g < r1, lane);
-      __syncthreads();
+    const TL<V>& L = A.lv[l];
+    for (int c = 0; c < L.ncol; ++c) {
+      const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
+      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 0>(L, base + gg, base + gg < r1, lane);
+      cluster_sync_all();
     }
-    for (int base = 0; base < L.nv; base += ng) row_pass<D, G, V, S, 2>(L, base + g, base + g < L.nv, lane);
-    __syncthreads();
-    const LV<V>& C = T->lv[l + 1];
-    for (int I = threadIdx.x; I < C.nv; I += blockDim.x) restrict_row<D, V>(L, C, I);
-    __syncthreads();
+    for (int base = 0; base < L.nv; base += NG) row_pass<D, G, V, S, 2>(L, base + gg, base + gg < L.nv, lane);
+    cluster_sync_all();
+    for (int I = tid; I < L.nvc; I += NT) restrict_row<D, V>(L, I);
+    cluster_sync_all();
   }
-  if (threadIdx.x < 32) coarse_solve_warp<V>(T->co, T->lv[Lc].b, T->lv[Lc].x);
-  __syncthreads();
+  if (rank == 0 && threadIdx.x < 32) coarse_solve_warp<V>(A.co, A.lv[Lc].b, A.lv[Lc].x);
+  cluster_sync_all();
   for (int l = Lc - 1; l >= l0; --l) {
-    const LV<V>& L = T->lv[l];
-    const LV<V>& C = T->lv[l + 1];
-    for (int i = threadIdx.x; i < L.nv; i += blockDim.x) prolong_row<D, V>(L, C, i);
-    __syncthreads();
-    const int* cs = T->cs[l];
-    for (int c = T->ncol[l] - 1; c >= 0; --c) {
-      const int r0 = cs[c], r1 = cs[c + 1];
-      for (int base = r0; base < r1; base += ng) row_pass<D, G, V, S, 1>(L, base + g, base + g < r1, lane);
-      __syncthreads();
+    const TL<V>& L = A.lv[l];
+    for (int i = tid; i < L.nv; i += NT) prolong_row<D, V>(L, i);
+    cluster_sync_all();
+    for (int c = L.ncol - 1; c >= 0; --c) {
+      const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
+      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 1>(L, base + gg, base + gg < r1, lane);
+      cluster_sync_all();
     }
   }
 }
@@ -282,11 +515,6 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const TailArgs<V>* _
 
 struct CGArgs {
   int nv;
-  long long nnz;
-  const int* rp;
-  const int* ci;
-  const double* off;       // planes [d*d][nnz]
-  const double* diag;      // planes [d*d][nv]
   const int* perm;         // solve index -> input vertex
   const uint8_t* isdir;    // input dof order
   const double* lift;      // input dof order
@@ -299,6 +527,14 @@ struct CGArgs {
   double* hist;            // relative residual history [max_iters]
   Scalars* sc;
   unsigned long long cond; // cudaGraphConditionalHandle (0 = none)
+  // SELL-32 level-0 operator (diagonal block included)
+  long long sell_n;        // padded rows (multiple of 32)
+  long long sell_tot;      // stored entries (plane stride)
+  const int* sell_rows;    // SELL position -> solve-order row (-1 = padding row)
+  const long long* sell_ptr;  // slice start [nslices]
+  const int* sell_w;       // slice width
+  const int* sell_ci;      // [sell_tot]
+  const double* sell_v;    // planes [d*d][sell_tot]
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -368,8 +604,10 @@ __global__ void __launch_bounds__(CG_THREADS) cg_init_kernel(CGArgs a, const dou
     s->rr = tot;
     s->relres = 1.0;
     s->iter = 0;
+    s->bodies = 0;
     s->first = 1;
     s->status = 0;
+    s->abort = 0;
     s->done = (s->res0 == 0.0) ? 1 : 0;
     if (s->done) s->relres = 0.0;
     set_cond(a.cond, s->done ? 0u : 1u);
@@ -382,9 +620,9 @@ __global__ void __launch_bounds__(CG_THREADS) rz_kernel(CGArgs a, const V* __res
   double acc = 0.0;
   const long long n = (long long)a.nv * D;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    acc += a.r[t] * (double)z[t];
-  // hard bound on loop bodies, independent of the reductions below: the
-  // device-side WHILE loop can never run more than max_iters + 2 bodies
+    acc += a.r[t] * (double)__ldcg(z + t);
+  // hard bound on loop bodies, independent of the reductions: the device-side
+  // WHILE loop never runs more than max_iters + 2 bodies
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Scalars* s = a.sc;
     s->bodies += 1;
@@ -408,51 +646,42 @@ __global__ void __launch_bounds__(CG_THREADS) p_update_kernel(CGArgs a, const V*
   const double beta = a.sc->beta;
   const long long n = (long long)a.nv * D;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    a.p[t] = (double)z[t] + beta * a.p[t];
+    a.p[t] = (double)__ldcg(z + t) + beta * a.p[t];
 }
 
-// q = A p (diagonal planes + off-diagonal planes), p.q, alpha = rho / p.q.
-template <int D, int G>
-__global__ void __launch_bounds__(CG_THREADS) spmv_dot_kernel(CGArgs a, int with_dot) {
-  const int lane = threadIdx.x & (G - 1);
-  const int gpb = CG_THREADS / G;
+// q = A p (SELL-32, one thread per row, one warp per slice), p.q, alpha.
+template <int D>
+__global__ void __launch_bounds__(CG_THREADS) spmv_sell_kernel(CGArgs a, int with_dot) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long nslices = a.sell_n >> 5;
   double dot = 0.0;
-  for (int base = blockIdx.x * gpb; base < a.nv; base += gridDim.x * gpb) {
-    const int row = base + (int)threadIdx.x / G;
-    const bool valid = row < a.nv;
-    int k0 = 0, k1 = 0;
-    if (valid) {
-      k0 = __ldg(a.rp + row);
-      k1 = __ldg(a.rp + row + 1);
-    }
+  for (long long s = warp; s < nslices; s += nwarps) {
+    const long long base = __ldg(a.sell_ptr + s) + lane;
+    const int w = __ldg(a.sell_w + s);
+    const int row = __ldg(a.sell_rows + (s << 5) + lane);
     double acc[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = 0.0;
-    if (valid && lane == 0) {
-#pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int bb = 0; bb < D; ++bb)
-          acc[c] += __ldg(a.diag + (long long)(c * D + bb) * a.nv + row) * a.p[(long long)row * D + bb];
-    }
-    for (int k = k0 + lane; k < k1; k += G) {
-      const int j = __ldg(a.ci + k);
+    for (int k = 0; k < w; ++k) {
+      const long long idx = base + ((long long)k << 5);
+      const int j = __ldg(a.sell_ci + idx);
       double pj[D];
 #pragma unroll
       for (int bb = 0; bb < D; ++bb) pj[bb] = a.p[(long long)j * D + bb];
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
-        for (int bb = 0; bb < D; ++bb) acc[c] += __ldg(a.off + (long long)(c * D + bb) * a.nnz + k) * pj[bb];
+        for (int bb = 0; bb < D; ++bb)
+          acc[c] = fma(__ldg(a.sell_v + (long long)(c * D + bb) * a.sell_tot + idx), pj[bb], acc[c]);
     }
+    if (row >= 0) {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, G);
-    if (valid && lane < D) {
-      const double qv = pick<D>(acc, lane);
-      a.q[(long long)row * D + lane] = qv;
-      dot += qv * a.p[(long long)row * D + lane];
+      for (int c = 0; c < D; ++c) {
+        a.q[(long long)row * D + c] = acc[c];
+        dot = fma(acc[c], a.p[(long long)row * D + c], dot);
+      }
     }
   }
   if (!with_dot) return;
@@ -474,7 +703,7 @@ __global__ void __launch_bounds__(CG_THREADS) spmv_dot_kernel(CGArgs a, int with
 // U += alpha p; r -= alpha q; ||r||; stop test; b_0 = (V) r.
 template <int D, typename V>
 __global__ void __launch_bounds__(CG_THREADS) cg_update_kernel(CGArgs a, V* b0) {
-  if (a.sc->done) return;  // breakdown in spmv_dot
+  if (a.sc->done) return;  // breakdown in spmv
   const double alpha = a.sc->alpha;
   double acc = 0.0;
   const long long n = (long long)a.nv * D;
@@ -492,7 +721,10 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update_kernel(CGArgs a, V* b0) 
     s->relres = sqrt(tot) / s->res0;
     s->iter += 1;
     if (s->iter <= s->max_iters) a.hist[s->iter - 1] = s->relres;
-    if (s->relres < s->tol) {
+    if (s->abort) {
+      s->done = 1;
+      s->status = VASMG_ERR_TIMEOUT;
+    } else if (s->relres < s->tol) {
       s->done = 1;
       s->status = VASMG_OK;
     } else if (!(s->relres == s->relres)) {
@@ -519,12 +751,109 @@ __global__ void cg_final_kernel(CGArgs a, double* __restrict__ Uout) {
   }
 }
 
+// ------------------------------------------------------------------ setup kernels for the engine
+
+__global__ void row2tile_kernel(const int* __restrict__ ts, int T, int* __restrict__ row2tile) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
+    for (int r = ts[t]; r < ts[t + 1]; ++r) row2tile[r] = t;
+}
+
+// dependency pairs (tile << 32 | neighbour tile), lower and upper parts
+__global__ void dep_pairs_kernel(const int* __restrict__ rp, const int* __restrict__ sp, const int* __restrict__ ci,
+                                 const int* __restrict__ row2tile, int nv, const long long* __restrict__ lo_off,
+                                 const long long* __restrict__ hi_off, u64* __restrict__ lo, u64* __restrict__ hi) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
+    const u64 t = (u64)row2tile[r];
+    long long ol = lo_off[r], oh = hi_off[r];
+    for (int k = rp[r]; k < sp[r]; ++k) lo[ol++] = (t << 32) | (u64)row2tile[ci[k]];
+    for (int k = sp[r]; k < rp[r + 1]; ++k) hi[oh++] = (t << 32) | (u64)row2tile[ci[k]];
+  }
+}
+
+__global__ void split_counts_kernel(const int* __restrict__ rp, const int* __restrict__ sp, int nv,
+                                    long long* __restrict__ lo, long long* __restrict__ hi) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
+    lo[r] = sp[r] - rp[r];
+    hi[r] = rp[r + 1] - sp[r];
+  }
+}
+
+__global__ void low32_e_kernel(const u64* __restrict__ k, i64 n, int* __restrict__ out) {
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    out[i] = (int)(k[i] & 0xffffffffull);
+}
+
+// SELL-32: rows sorted by length (longest first) inside windows of 1024 rows
+__global__ void sell_keys_kernel(const int* __restrict__ rp, int nv, u64* __restrict__ keys, int* __restrict__ vals) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
+    const u64 len = (u64)(rp[r + 1] - rp[r] + 1);  // + diagonal
+    keys[r] = ((u64)(r >> 10) << 40) | ((1023ull - len) << 30) | (u64)(r & 1023);
+    vals[r] = r;
+  }
+}
+
+__global__ void sell_width_kernel(const int* __restrict__ rows, const int* __restrict__ rp, long long nslices,
+                                  int nv, int* __restrict__ w, long long* __restrict__ wbytes) {
+  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nslices;
+       s += (long long)gridDim.x * blockDim.x) {
+    int m = 0;
+    for (int l = 0; l < 32; ++l) {
+      const long long i = s * 32 + l;
+      if (i < nv) {
+        const int r = rows[i];
+        m = max(m, rp[r + 1] - rp[r] + 1);
+      }
+    }
+    w[s] = m;
+    wbytes[s] = (long long)m * 32;
+  }
+}
+
+template <int D>
+__global__ void sell_fill_kernel(const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                 const double* __restrict__ off, long long nnz, const double* __restrict__ diag, int nv,
+                                 long long nslices, const long long* __restrict__ ptr, const int* __restrict__ w,
+                                 long long tot, int* __restrict__ sci, double* __restrict__ sv,
+                                 int* __restrict__ srow) {
+  constexpr int DD = D * D;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nslices * 32;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long s = i >> 5;
+    const int lane = (int)(i & 31);
+    const int r = i < nv ? rows[i] : -1;
+    srow[i] = r;
+    const int width = w[s];
+    for (int k = 0; k < width; ++k) {
+      const long long idx = ptr[s] + (long long)k * 32 + lane;
+      int col;
+      double blk[DD];
+      if (r < 0) {
+        col = 0;
+        for (int q = 0; q < DD; ++q) blk[q] = 0.0;
+      } else if (k == 0) {
+        col = r;
+        for (int q = 0; q < DD; ++q) blk[q] = diag[(long long)q * nv + r];
+      } else if (rp[r] + k - 1 < rp[r + 1]) {
+        const long long e = rp[r] + k - 1;
+        col = ci[e];
+        for (int q = 0; q < DD; ++q) blk[q] = off[(long long)q * nnz + e];
+      } else {
+        col = r;
+        for (int q = 0; q < DD; ++q) blk[q] = 0.0;
+      }
+      sci[idx] = col;
+      for (int q = 0; q < DD; ++q) sv[(long long)q * tot + idx] = blk[q];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ conversions for vasmg_apply
 
 template <typename V>
 __global__ void to_solve_kernel(const double* __restrict__ in, V* __restrict__ out, const int* __restrict__ perm,
                                 long long nv, int d) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nv * d; t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nv * d;
+       t += (long long)gridDim.x * blockDim.x) {
     const long long r = t / d;
     out[t] = (V)in[(long long)perm[r] * d + (t - r * d)];
   }
@@ -532,7 +861,8 @@ __global__ void to_solve_kernel(const double* __restrict__ in, V* __restrict__ o
 template <typename V>
 __global__ void from_solve_kernel(const V* __restrict__ in, double* __restrict__ out, const int* __restrict__ perm,
                                   long long nv, int d) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nv * d; t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nv * d;
+       t += (long long)gridDim.x * blockDim.x) {
     const long long r = t / d;
     out[(long long)perm[r] * d + (t - r * d)] = (double)in[t];
   }
@@ -559,22 +889,29 @@ struct Engine : EngineBase {
   Ctx* c = nullptr;
   int L = 0;       // number of levels
   int lt = 0;      // first tail level
+  int nct = 1;     // CTAs in the tail cluster
   std::vector<LV<V>> lv;
   std::vector<int> G;
-  std::vector<DevBuf<int32_t>> cs_dev;
-  DevBuf<TailArgs<V>> tail;
+  std::vector<DevBuf<int32_t>> cs_dev, ts_dev, dlo_rp, dlo, dhi_rp, dhi;
+  std::vector<DevBuf<unsigned>> fl_down, fl_up;
+  std::vector<int> grid_down, grid_up;
+  DevBuf<int> ctrs;
   DevBuf<double> coarse_y;
   // CG
   DevBuf<double> U, r, p, q, part, hist, Fbuf, Ubuf;
   DevBuf<Scalars> sc;
+  DevBuf<int32_t> sell_rows, sell_w, sell_ci;
+  DevBuf<long long> sell_ptr;
+  DevBuf<double> sell_v;
+  i64 sell_real_entries = 0;
   Scalars* host_sc = nullptr;
   CGArgs cga{};
-  int cg_blocks = 0, spmv_blocks = 0, G0 = 8;
+  int cg_blocks = 0, spmv_blocks = 0;
   CoarseArgs co{};
   // graphs
   cudaGraphExec_t exec_while = nullptr;
   cudaGraphExec_t exec_body = nullptr;
-  i64 launches_body = 0, launches_outer = 0;
+  i64 launches_body = 0;
   i64 launch_counter = 0;
 
   explicit Engine(Ctx& ctx) : c(&ctx) { build(); }
@@ -602,13 +939,128 @@ struct Engine : EngineBase {
     return (const V*)s.rw32.get();
   }
 
+  // tiles of one level: rows of a colour cut into pieces of two CTA passes
+  void build_tiles(int l) {
+    cudaStream_t s = c->stream;
+    SolveLevel& sl = c->S[l];
+    const int rows_per_tile = 2 * (DF_THREADS / G[l]);
+    std::vector<int> ts;
+    for (int col = 0; col < sl.ncol; ++col)
+      for (int r0 = sl.cs[col]; r0 < sl.cs[col + 1]; r0 += rows_per_tile) ts.push_back(r0);
+    ts.push_back((int)sl.nv);
+    const int T = (int)ts.size() - 1;
+    ts_dev[l].alloc(T + 1, s);
+    ts_dev[l].upload(ts.data(), T + 1);
+    fl_down[l].alloc(T, s);
+    fl_up[l].alloc(T, s);
+    fl_down[l].zero();
+    fl_up[l].zero();
+    DevBuf<int32_t> row2tile;
+    row2tile.alloc(sl.nv, s);
+    row2tile_kernel<<<grid_for(T, 128), 128, 0, s>>>(ts_dev[l].get(), T, row2tile.get());
+    check_launch("row2tile");
+    DevBuf<long long> clo, chi;
+    clo.alloc(sl.nv + 1, s);
+    chi.alloc(sl.nv + 1, s);
+    clo.zero();
+    chi.zero();
+    split_counts_kernel<<<grid_for(sl.nv, 256), 256, 0, s>>>(sl.rp.get(), sl.sp.get(), (int)sl.nv, clo.get(),
+                                                              chi.get());
+    check_launch("split_counts");
+    scan_exclusive_i64((const i64*)clo.get(), (i64*)clo.get(), sl.nv + 1, s);
+    scan_exclusive_i64((const i64*)chi.get(), (i64*)chi.get(), sl.nv + 1, s);
+    const i64 nlo = fetch(clo.get() + sl.nv, s), nhi = fetch(chi.get() + sl.nv, s);
+    DevBuf<u64> klo, khi;
+    klo.alloc(std::max<i64>(nlo, 1), s);
+    khi.alloc(std::max<i64>(nhi, 1), s);
+    dep_pairs_kernel<<<grid_for(sl.nv, 256), 256, 0, s>>>(sl.rp.get(), sl.sp.get(), sl.ci.get(), row2tile.get(),
+                                                          (int)sl.nv, clo.get(), chi.get(), klo.get(), khi.get());
+    check_launch("dep_pairs");
+    auto finish = [&](DevBuf<u64>& k, i64 n, DevBuf<int32_t>& rp, DevBuf<int32_t>& lst) {
+      radix_sort(k.get(), nullptr, n, 32 + bits_for((u64)T), s);
+      const i64 m = unique_sorted(k.get(), n, s);
+      rp.alloc(T + 1, s);
+      rowptr_from_pairs(k.get(), m, T, rp.get(), s);
+      lst.alloc(std::max<i64>(m, 1), s);
+      if (m > 0) {
+        low32_e_kernel<<<grid_for(m, 256), 256, 0, s>>>(k.get(), m, lst.get());
+        check_launch("dep_low32");
+      }
+    };
+    finish(klo, nlo, dlo_rp[l], dlo[l]);
+    finish(khi, nhi, dhi_rp[l], dhi[l]);
+    lv[l].T = T;
+    lv[l].ts = ts_dev[l].get();
+    lv[l].dlo_rp = dlo_rp[l].get();
+    lv[l].dlo = dlo[l].get();
+    lv[l].dhi_rp = dhi_rp[l].get();
+    lv[l].dhi = dhi[l].get();
+    lv[l].fl_down = fl_down[l].get();
+    lv[l].fl_up = fl_up[l].get();
+  }
+
+  void build_sell() {
+    cudaStream_t s = c->stream;
+    SolveLevel& s0 = c->S[0];
+    const int nv = (int)s0.nv;
+    DevBuf<u64> keys;
+    keys.alloc(nv, s);
+    DevBuf<int32_t> rows;
+    rows.alloc(nv, s);
+    sell_keys_kernel<<<grid_for(nv, 256), 256, 0, s>>>(s0.rp.get(), nv, keys.get(), rows.get());
+    check_launch("sell_keys");
+    radix_sort(keys.get(), rows.get(), nv, 64, s);
+    const long long nslices = ceil_div(nv, 32);
+    sell_w.alloc(nslices, s);
+    DevBuf<long long> wb;
+    wb.alloc(nslices + 1, s);
+    wb.zero();
+    sell_width_kernel<<<grid_for(nslices, 256), 256, 0, s>>>(rows.get(), s0.rp.get(), nslices, nv, sell_w.get(),
+                                                             wb.get());
+    check_launch("sell_width");
+    scan_exclusive_i64((const i64*)wb.get(), (i64*)wb.get(), nslices + 1, s);
+    const long long tot = fetch(wb.get() + nslices, s);
+    sell_ptr = std::move(wb);
+    sell_ci.alloc(tot, s);
+    sell_v.alloc((i64)D * D * tot, s);
+    sell_rows.alloc(nslices * 32, s);
+    sell_fill_kernel<D><<<grid_for(nslices * 32, 256), 256, 0, s>>>(
+        rows.get(), s0.rp.get(), s0.ci.get(), s0.off64.get(), s0.nnz, s0.diag64.get(), nv, nslices, sell_ptr.get(),
+        sell_w.get(), tot, sell_ci.get(), sell_v.get(), sell_rows.get());
+    check_launch("sell_fill");
+    sell_real_entries = s0.nnz + s0.nv;
+    cga.sell_n = nslices * 32;
+    cga.sell_tot = tot;
+    cga.sell_rows = sell_rows.get();
+    cga.sell_ptr = sell_ptr.get();
+    cga.sell_w = sell_w.get();
+    cga.sell_ci = sell_ci.get();
+    cga.sell_v = sell_v.get();
+  }
+
   void build() {
     cudaStream_t s = c->stream;
     L = (int)c->S.size();
     VASMG_CHECK(L <= MAX_LEVELS, VASMG_ERR_UNSUPPORTED, "too many levels");
-    lv.resize(L);
+    lv.assign(L, LV<V>{});
     G.resize(L);
     cs_dev.resize(L);
+    ts_dev.resize(L);
+    dlo_rp.resize(L);
+    dlo.resize(L);
+    dhi_rp.resize(L);
+    dhi.resize(L);
+    fl_down.resize(L);
+    fl_up.resize(L);
+    ctrs.alloc((i64)L * C_N, s);
+    {
+      std::vector<int> h((size_t)L * C_N, 0);
+      for (int l = 0; l < L; ++l) {
+        h[l * C_N + C_DEPOCH] = 1;
+        h[l * C_N + C_UEPOCH] = 1;
+      }
+      ctrs.upload(h.data(), (i64)L * C_N);
+    }
     for (int l = 0; l < L; ++l) {
       SolveLevel& sl = c->S[l];
       const i64 n = sl.nv * D;
@@ -622,6 +1074,7 @@ struct Engine : EngineBase {
       cs_dev[l].upload(sl.cs.data(), sl.ncol + 1);
       LV<V>& v = lv[l];
       v.nv = (int)sl.nv;
+      v.ncol = sl.ncol;
       v.nnz = sl.nnz;
       v.rp = sl.rp.get();
       v.ci = sl.ci.get();
@@ -632,16 +1085,74 @@ struct Engine : EngineBase {
       v.x = (V*)sl.x.get();
       v.b = (V*)sl.b.get();
       v.r = (V*)sl.r.get();
+      v.cs = cs_dev[l].get();
+      v.ctr = ctrs.get() + (i64)l * C_N;
+      G[l] = pick_G(sl.nv > 0 ? (double)sl.nnz / (double)sl.nv : 1.0);
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+      SolveLevel& sl = c->S[l];
+      LV<V>& v = lv[l];
+      v.nvc = (int)c->S[l + 1].nv;
       v.prp = sl.prp.get();
       v.pci = sl.pci.get();
       v.pw = pw_ptr(sl);
       v.rrp = sl.rrp.get();
       v.rci = sl.rci.get();
       v.rw = rw_ptr(sl);
-      G[l] = pick_G(sl.nv > 0 ? (double)sl.nnz / (double)sl.nv : 1.0);
+      v.bc = lv[l + 1].b;
+      v.xc = lv[l + 1].x;
+      build_tiles(l);
     }
     lt = L - 1;
     while (lt > 0 && c->S[lt - 1].nv <= TAIL_NV) --lt;
+    // occupancy-sized grids for the self-scheduling launches
+    int dev = 0, sms = 0;
+    VASMG_CUDA(cudaGetDevice(&dev));
+    VASMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid_down.assign(L, 1);
+    grid_up.assign(L, 1);
+    for (int l = 0; l + 1 < L; ++l) {
+      int bd = 1, bu = 1;
+      switch (G[l]) {
+        case 4: occ<4>(&bd, &bu); break;
+        case 8: occ<8>(&bd, &bu); break;
+        case 16: occ<16>(&bd, &bu); break;
+        default: occ<32>(&bd, &bu); break;
+      }
+      const int work_d = 2 * lv[l].T + (int)ceil_div(lv[l].nvc, RC_ROWS);
+      const int work_u = lv[l].T + (int)ceil_div(lv[l].nv, RP_ROWS);
+      grid_down[l] = std::max(1, std::min(bd * sms, work_d));
+      grid_up[l] = std::max(1, std::min(bu * sms, work_u));
+    }
+    // tail cluster size: as many CTAs (<= 16) as the work of the tail levels warrants
+    {
+      i64 work = 0;
+      for (int l = lt; l < L; ++l) work += c->S[l].nnz;
+      nct = 1;
+      while (nct < 16 && work > (i64)nct * 4 * TAIL_THREADS * 8) nct *= 2;
+      if (nct > 8)
+        if (cudaFuncSetAttribute(tail_kernel<D, V, S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+          nct = 8;
+      cudaGetLastError();
+      while (nct > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nct);
+        cfg.blockDim = dim3(TAIL_THREADS);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = nct;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, tail_kernel<D, V, S>, &cfg) == cudaSuccess && nclusters > 0)
+          break;
+        cudaGetLastError();
+        nct /= 2;
+      }
+    }
     // coarsest
     coarse_y.alloc(c->nc, s);
     co.chol = c->chol.get();
@@ -650,20 +1161,6 @@ struct Engine : EngineBase {
     co.y = coarse_y.get();
     co.n = (int)c->nc;
     co.d = D;
-    {
-      std::vector<char> hbuf(sizeof(TailArgs<V>), 0);
-      TailArgs<V>* ta = (TailArgs<V>*)hbuf.data();
-      ta->l0 = lt;
-      ta->L = L - 1;
-      for (int l = 0; l < L; ++l) {
-        ta->lv[l] = lv[l];
-        ta->cs[l] = cs_dev[l].get();
-        ta->ncol[l] = c->S[l].ncol;
-      }
-      ta->co = co;
-      tail.alloc(1, s);
-      VASMG_CUDA(cudaMemcpyAsync(tail.get(), hbuf.data(), sizeof(TailArgs<V>), cudaMemcpyHostToDevice, s));
-    }
     // CG state
     SolveLevel& s0 = c->S[0];
     const i64 n = s0.nv * D;
@@ -674,23 +1171,14 @@ struct Engine : EngineBase {
     Fbuf.alloc(n, s);
     Ubuf.alloc(n, s);
     p.zero();
-    int dev = 0, sms = 0;
-    VASMG_CUDA(cudaGetDevice(&dev));
-    VASMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cg_blocks = (int)std::max<i64>(1, std::min<i64>((i64)sms * 8, ceil_div(n, CG_THREADS)));
-    G0 = pick_G((double)s0.nnz / std::max<i64>(1, s0.nv) + 1.0);
-    spmv_blocks = (int)std::max<i64>(1, std::min<i64>((i64)sms * 8, ceil_div(s0.nv, CG_THREADS / G0)));
+    spmv_blocks = (int)std::max<i64>(1, std::min<i64>((i64)sms * 8, ceil_div(s0.nv, CG_THREADS)));
     part.alloc(std::max(cg_blocks, spmv_blocks), s);
     hist.alloc(std::max(1, c->max_iters), s);
     sc.alloc(1, s);
     sc.zero();
     VASMG_CUDA(cudaMallocHost((void**)&host_sc, sizeof(Scalars)));
     cga.nv = (int)s0.nv;
-    cga.nnz = s0.nnz;
-    cga.rp = s0.rp.get();
-    cga.ci = s0.ci.get();
-    cga.off = s0.off64.get();
-    cga.diag = s0.diag64.get();
     cga.perm = s0.perm.get();
     cga.isdir = c->isdir.get();
     cga.lift = c->lift.get();
@@ -703,85 +1191,96 @@ struct Engine : EngineBase {
     cga.hist = hist.get();
     cga.sc = sc.get();
     cga.cond = 0;
+    build_sell();
     VASMG_CUDA(cudaStreamSynchronize(s));
   }
 
+  template <int GG>
+  void occ(int* bd, int* bu) {
+    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bd, vdown_kernel<D, GG, V, S>, DF_THREADS, 0));
+    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bu, vup_kernel<D, GG, V, S>, DF_THREADS, 0));
+  }
+
   // ---------------------------------------------------------------- launches
-  template <int MODE>
-  void colour_launch(int l, int row0, int row1, cudaStream_t s) {
-    if (row1 <= row0) return;
-    const int g = G[l];
-    const i64 threads = (i64)(row1 - row0) * g;
-    const int blocks = (int)ceil_div(threads, 256);
-    switch (g) {
-      case 4: colour_kernel<D, 4, V, S, MODE><<<blocks, 256, 0, s>>>(lv[l], row0, row1); break;
-      case 8: colour_kernel<D, 8, V, S, MODE><<<blocks, 256, 0, s>>>(lv[l], row0, row1); break;
-      case 16: colour_kernel<D, 16, V, S, MODE><<<blocks, 256, 0, s>>>(lv[l], row0, row1); break;
-      default: colour_kernel<D, 32, V, S, MODE><<<blocks, 256, 0, s>>>(lv[l], row0, row1); break;
+  void down(int l, int phases, cudaStream_t s) {
+    const int g = grid_down[l];
+    switch (G[l]) {
+      case 4: vdown_kernel<D, 4, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
+      case 8: vdown_kernel<D, 8, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
+      case 16: vdown_kernel<D, 16, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
+      default: vdown_kernel<D, 32, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
     }
     ++launch_counter;
   }
-  void sweep_fwd_zero(int l, cudaStream_t s) {
-    const auto& cs = c->S[l].cs;
-    for (int col = 0; col < c->S[l].ncol; ++col) colour_launch<0>(l, cs[col], cs[col + 1], s);
-  }
-  void sweep_bwd(int l, cudaStream_t s) {
-    const auto& cs = c->S[l].cs;
-    for (int col = c->S[l].ncol - 1; col >= 0; --col) colour_launch<1>(l, cs[col], cs[col + 1], s);
-  }
-  void residual(int l, cudaStream_t s) { colour_launch<2>(l, 0, lv[l].nv, s); }
-  void restrict_to(int l, cudaStream_t s) {
-    restrict_kernel<D, V><<<grid_for(lv[l + 1].nv, 256), 256, 0, s>>>(lv[l], lv[l + 1]);
+  void up(int l, int phases, cudaStream_t s) {
+    const int g = grid_up[l];
+    switch (G[l]) {
+      case 4: vup_kernel<D, 4, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
+      case 8: vup_kernel<D, 8, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
+      case 16: vup_kernel<D, 16, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
+      default: vup_kernel<D, 32, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
+    }
     ++launch_counter;
   }
-  void prolong_from(int l, cudaStream_t s) {
-    prolong_kernel<D, V><<<grid_for(lv[l].nv, 256), 256, 0, s>>>(lv[l], lv[l + 1]);
-    ++launch_counter;
-  }
-  void tail_launch(cudaStream_t s) {
-    tail_kernel<D, V, S><<<1, TAIL_THREADS, 0, s>>>(tail.get());
+  void tail(int l0, cudaStream_t s) {
+    TailArgs<V> ta;
+    std::memset(&ta, 0, sizeof(ta));
+    ta.l0 = l0;
+    ta.L = L - 1;
+    for (int l = 0; l < L; ++l) {
+      const LV<V>& v = lv[l];
+      TL<V>& t = ta.lv[l];
+      t.nv = v.nv;
+      t.nnz = v.nnz;
+      t.rp = v.rp;
+      t.ci = v.ci;
+      t.sp = v.sp;
+      t.off = v.off;
+      t.dinv = v.dinv;
+      t.dead = v.dead;
+      t.x = v.x;
+      t.b = v.b;
+      t.r = v.r;
+      t.cs = v.cs;
+      t.ncol = v.ncol;
+      t.nvc = v.nvc;
+      t.prp = v.prp;
+      t.pci = v.pci;
+      t.pw = v.pw;
+      t.rrp = v.rrp;
+      t.rci = v.rci;
+      t.rw = v.rw;
+      t.bc = v.bc;
+      t.xc = v.xc;
+    }
+    ta.co = co;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nct);
+    cfg.blockDim = dim3(TAIL_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = nct;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    VASMG_CUDA(cudaLaunchKernelEx(&cfg, tail_kernel<D, V, S>, ta));
     ++launch_counter;
   }
   // V-cycle from level l0 (b_{l0} set, result in x_{l0}).
   void vcycle(int l0, cudaStream_t s) {
     if (l0 >= lt) {
-      if (l0 == lt) {
-        tail_launch(s);
-        return;
-      }
-      // a V-cycle starting inside the tail range: run per level for exactness
-      for (int l = l0; l < L - 1; ++l) {
-        sweep_fwd_zero(l, s);
-        residual(l, s);
-        restrict_to(l, s);
-      }
-      coarse_kernel<V><<<1, 32, 0, s>>>(co, lv[L - 1].b, lv[L - 1].x);
-      ++launch_counter;
-      for (int l = L - 2; l >= l0; --l) {
-        prolong_from(l, s);
-        sweep_bwd(l, s);
-      }
+      tail(l0, s);
       return;
     }
-    for (int l = l0; l < lt; ++l) {
-      sweep_fwd_zero(l, s);
-      residual(l, s);
-      restrict_to(l, s);
-    }
-    tail_launch(s);
-    for (int l = lt - 1; l >= l0; --l) {
-      prolong_from(l, s);
-      sweep_bwd(l, s);
-    }
+    for (int l = l0; l < lt; ++l) down(l, 7, s);
+    tail(lt, s);
+    for (int l = lt - 1; l >= l0; --l) up(l, 3, s);
   }
 
   void spmv(cudaStream_t s, int with_dot) {
-    switch (G0) {
-      case 4: spmv_dot_kernel<D, 4><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot); break;
-      case 8: spmv_dot_kernel<D, 8><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot); break;
-      case 16: spmv_dot_kernel<D, 16><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot); break;
-      default: spmv_dot_kernel<D, 32><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot); break;
-    }
+    spmv_sell_kernel<D><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot);
     ++launch_counter;
   }
 
@@ -832,8 +1331,12 @@ struct Engine : EngineBase {
         ok = cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
              cudaSuccess;
         if (ok) {
-          body(s);
-          ok = cudaStreamEndCapture(s, &out) == cudaSuccess;
+          try {
+            body(s);
+          } catch (...) {
+            ok = false;
+          }
+          ok = (cudaStreamEndCapture(s, &out) == cudaSuccess) && ok;
         }
         launches_body = launch_counter;
       }
@@ -879,7 +1382,6 @@ struct Engine : EngineBase {
     init.max_iters = c->max_iters;
     VASMG_CUDA(cudaMemcpyAsync(sc.get(), &init, sizeof(Scalars), cudaMemcpyHostToDevice, s));
     VASMG_CUDA(cudaMemcpyAsync(Fbuf.get(), F, sizeof(double) * n, cudaMemcpyDefault, s));
-    i64 launches = 0;
     if (exec_while) {
       VASMG_CUDA(cudaGraphLaunch(exec_while, s));
       VASMG_CUDA(cudaMemcpyAsync(host_sc, sc.get(), sizeof(Scalars), cudaMemcpyDeviceToHost, s));
@@ -901,8 +1403,7 @@ struct Engine : EngineBase {
     VASMG_CUDA(cudaMemcpyAsync(Uout, Ubuf.get(), sizeof(double) * n, cudaMemcpyDefault, s));
     VASMG_CUDA(cudaStreamSynchronize(s));
     const int iters = host_sc->iter;
-    launches = 2 + launches_body * (i64)iters;
-    ctx.last_launches = launches;
+    ctx.last_launches = 2 + launches_body * (i64)iters;
     if (st) {
       st->iterations = iters;
       st->rel_res = host_sc->relres;
@@ -912,6 +1413,7 @@ struct Engine : EngineBase {
         if (k > 0) VASMG_CUDA(cudaMemcpy(st->res_history, hist.get(), sizeof(double) * k, cudaMemcpyDeviceToHost));
       }
     }
+    if (host_sc->abort) return VASMG_ERR_TIMEOUT;
     return host_sc->status;
   }
 
@@ -922,10 +1424,19 @@ struct Engine : EngineBase {
   void from_solve(const V* in, double* y, int l, cudaStream_t s) {
     from_solve_kernel<V><<<grid_for((i64)lv[l].nv * D, 256), 256, 0, s>>>(in, y, c->S[l].perm.get(), lv[l].nv, D);
   }
+  void clear_abort(cudaStream_t s) { VASMG_CUDA(cudaMemsetAsync(&sc.get()->abort, 0, sizeof(int), s)); }
+  int read_abort(cudaStream_t s) {
+    int a = 0;
+    VASMG_CUDA(cudaMemcpyAsync(&a, &sc.get()->abort, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VASMG_CUDA(cudaStreamSynchronize(s));
+    return a;
+  }
 
   void apply(Ctx& ctx, int op, int l, const double* x, double* y) override {
     cudaStream_t s = c->stream;
     VASMG_CHECK(l >= 0 && l < L, VASMG_ERR_INVALID_ARG, "level out of range");
+    const bool has_coarser = l + 1 < L;
+    clear_abort(s);
     switch (op) {
       case VASMG_OP_MATVEC: {
         VASMG_CHECK(l == 0, VASMG_ERR_INVALID_ARG, "MATVEC runs the level-0 FP64 operator");
@@ -938,33 +1449,35 @@ struct Engine : EngineBase {
         break;
       }
       case VASMG_OP_SMOOTH_FWD:
+        VASMG_CHECK(has_coarser, VASMG_ERR_INVALID_ARG, "the coarsest level is solved directly");
         to_solve(x, lv[l].b, l, s);
-        sweep_fwd_zero(l, s);
+        down(l, 1, s);
         from_solve(lv[l].x, y, l, s);
         break;
       case VASMG_OP_SMOOTH_BWD:
+        VASMG_CHECK(has_coarser, VASMG_ERR_INVALID_ARG, "the coarsest level is solved directly");
         to_solve(x, lv[l].b, l, s);
         to_solve(y, lv[l].x, l, s);
-        sweep_bwd(l, s);
+        up(l, 2, s);
         from_solve(lv[l].x, y, l, s);
         break;
       case VASMG_OP_RESIDUAL:
+        VASMG_CHECK(has_coarser, VASMG_ERR_INVALID_ARG, "the coarsest level is solved directly");
         to_solve(x, lv[l].b, l, s);
-        sweep_fwd_zero(l, s);
-        residual(l, s);
+        down(l, 3, s);
         from_solve(lv[l].r, y, l, s);
         break;
       case VASMG_OP_RESTRICT:
-        VASMG_CHECK(l + 1 < L, VASMG_ERR_INVALID_ARG, "no coarser level");
+        VASMG_CHECK(has_coarser, VASMG_ERR_INVALID_ARG, "no coarser level");
         to_solve(x, lv[l].r, l, s);
-        restrict_to(l, s);
+        down(l, 4, s);
         from_solve(lv[l + 1].b, y, l + 1, s);
         break;
       case VASMG_OP_PROLONG:
-        VASMG_CHECK(l + 1 < L, VASMG_ERR_INVALID_ARG, "no coarser level");
+        VASMG_CHECK(has_coarser, VASMG_ERR_INVALID_ARG, "no coarser level");
         to_solve(x, lv[l + 1].x, l + 1, s);
         to_solve(y, lv[l].x, l, s);
-        prolong_from(l, s);
+        up(l, 1, s);
         from_solve(lv[l].x, y, l, s);
         break;
       case VASMG_OP_COARSE:
@@ -982,45 +1495,68 @@ struct Engine : EngineBase {
     }
     check_launch("apply");
     VASMG_CUDA(cudaStreamSynchronize(s));
+    VASMG_CHECK(read_abort(s) == 0, VASMG_ERR_TIMEOUT, "a device wait gave up");
     (void)ctx;
   }
 
   // ---------------------------------------------------------------- timing
+  // Algorithmic bytes: every array the step must touch, each element once.
+  double pass_bytes(int l) {  // one pass over the off-diagonal blocks + row pointers
+    const SolveLevel& sl = c->S[l];
+    return (double)sl.nnz * (D * D * sizeof(S) + 4.0) + (sl.nv + 1.0) * 4.0 + (double)sl.nv * 4.0;
+  }
+  double down_bytes(int l) {
+    const SolveLevel& sl = c->S[l];
+    const double n = (double)sl.nv * D;
+    double b = pass_bytes(l) + (double)sl.nv * D * D * sizeof(V) + 4.0 * n * sizeof(V);  // b, x w+r, r w
+    if (l + 1 < L) {
+      const double pn = (double)c->C[l].pnnz;
+      b += n * sizeof(V) + pn * (4.0 + sizeof(V)) + (c->S[l + 1].nv + 1.0) * 4.0 +
+           (double)c->S[l + 1].nv * D * sizeof(V);
+    }
+    return b;
+  }
   double sweep_bytes(int l) {
     const SolveLevel& sl = c->S[l];
     const double n = (double)sl.nv * D;
-    return (double)sl.nnz * (D * D * sizeof(S) + 4.0) + (sl.nv + 1.0) * 4.0 + (double)sl.nv * D * D * sizeof(V) +
-           3.0 * n * sizeof(V);
+    return pass_bytes(l) + (double)sl.nv * D * D * sizeof(V) + 3.0 * n * sizeof(V);  // b, x r+w
+  }
+  double up_bytes(int l) {
+    double b = sweep_bytes(l);
+    if (l + 1 < L) {
+      const double pn = (double)c->C[l].pnnz;
+      b += pn * (4.0 + sizeof(V)) + (c->S[l].nv + 1.0) * 4.0 + (double)c->S[l].nv +
+           (double)c->S[l + 1].nv * D * sizeof(V) + 2.0 * (double)c->S[l].nv * D * sizeof(V);
+    }
+    return b;
   }
   double spmv_bytes() {
     const SolveLevel& sl = c->S[0];
     const double n = (double)sl.nv * D;
-    return (double)sl.nnz * (D * D * 8.0 + 4.0) + (sl.nv + 1.0) * 4.0 + (double)sl.nv * D * D * 8.0 + 2.0 * n * 8.0;
+    return (double)sell_real_entries * (D * D * 8.0 + 4.0) + 3.0 * n * 8.0;  // blocks, p read, q write, p for the dot
   }
   double vcycle_bytes() {
     double b = 0;
-    for (int l = 0; l < L - 1; ++l) {
-      const SolveLevel& sl = c->S[l];
-      const double n = (double)sl.nv * D;
-      // pre-smooth + residual: one pass over the off-diagonal blocks; post-smooth: one pass
-      b += 2.0 * ((double)sl.nnz * (D * D * sizeof(S) + 4.0) + (sl.nv + 1.0) * 8.0);
-      b += 2.0 * (double)sl.nv * D * D * sizeof(V);     // diagonal inverses, twice
-      b += 7.0 * n * sizeof(V);                          // b, x twice each; r write+read; prolong x rmw
-      const double pn = (double)c->C[l].pnnz;
-      b += 2.0 * pn * (4.0 + sizeof(V)) + 2.0 * (sl.nv + 1.0) * 4.0;  // P and R
-    }
+    for (int l = 0; l + 1 < L; ++l) b += down_bytes(l) + up_bytes(l);
     return b;
   }
 
   double time(Ctx& ctx, int which, int level, int reps, double* bytes) override {
     cudaStream_t s = c->stream;
+    VASMG_CHECK(which == VASMG_KERNEL_SPMV64 || which == VASMG_KERNEL_VCYCLE || level + 1 < L, VASMG_ERR_INVALID_ARG,
+                "the coarsest level has no sweep");
+    clear_abort(s);
     cudaEvent_t e0, e1;
     VASMG_CUDA(cudaEventCreate(&e0));
     VASMG_CUDA(cudaEventCreate(&e1));
     auto run = [&]() {
-      if (which == VASMG_KERNEL_SPMV64) spmv(s, 0);
-      else if (which == VASMG_KERNEL_SWEEP) sweep_bwd(level, s);
-      else vcycle(0, s);
+      switch (which) {
+        case VASMG_KERNEL_SPMV64: spmv(s, 0); break;
+        case VASMG_KERNEL_SWEEP: up(level, 2, s); break;
+        case VASMG_KERNEL_DOWN: down(level, 7, s); break;
+        case VASMG_KERNEL_UP: up(level, 3, s); break;
+        default: vcycle(0, s); break;
+      }
     };
     run();
     VASMG_CUDA(cudaStreamSynchronize(s));
@@ -1032,7 +1568,14 @@ struct Engine : EngineBase {
     VASMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    *bytes = which == VASMG_KERNEL_SPMV64 ? spmv_bytes() : (which == VASMG_KERNEL_SWEEP ? sweep_bytes(level) : vcycle_bytes());
+    VASMG_CHECK(read_abort(s) == 0, VASMG_ERR_TIMEOUT, "a device wait gave up");
+    switch (which) {
+      case VASMG_KERNEL_SPMV64: *bytes = spmv_bytes(); break;
+      case VASMG_KERNEL_SWEEP: *bytes = sweep_bytes(level); break;
+      case VASMG_KERNEL_DOWN: *bytes = down_bytes(level); break;
+      case VASMG_KERNEL_UP: *bytes = up_bytes(level); break;
+      default: *bytes = vcycle_bytes(); break;
+    }
     (void)ctx;
     return (double)ms / reps;
   }

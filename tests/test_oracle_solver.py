@@ -20,6 +20,26 @@ def _reduced_rhs(o, p):
     return F
 
 
+def _priority(o, l, nv, dim):
+    """Colouring priority: splitmix64 on the fine level; on coarser levels the
+    lattice class sum_a ((p_a/u) mod 3) 3^a first (class 0 highest), u the
+    side of the level's smallest cell."""
+    from tests.helpers import K_of, deinterleave
+
+    sm = meshgen.splitmix64(np.arange(nv, dtype=np.uint64))
+    if l == 0:
+        return sm
+    K = K_of(dim)
+    D = int(o.cells(l)[:, 0].max())
+    q = deinterleave(o.lattice(l), dim, K + 1) >> np.uint64(K - D)
+    cls = np.zeros(nv, dtype=np.uint64)
+    w = 1
+    for a in range(dim):
+        cls += (q[:, a] % np.uint64(3)) * np.uint64(w)
+        w *= 3
+    return ((np.uint64(w - 1) - cls) << np.uint64(58)) | (sm >> np.uint64(6))
+
+
 @pytest.mark.parametrize("dim,n,seed", [(2, 10, 1), (3, 5, 2)])
 def test_colouring_is_proper_and_greedy_by_priority(oracle_mod, dim, n, seed):
     p = _prob(dim, n, seed)
@@ -28,15 +48,31 @@ def test_colouring_is_proper_and_greedy_by_priority(oracle_mod, dim, n, seed):
         rp, ci, _ = o.operator(l)
         col = o.colours(l)
         nv = len(rp) - 1
-        prio = meshgen.splitmix64(np.arange(nv, dtype=np.uint64))
+        prio = _priority(o, l, nv, dim)
         for i in range(nv):
             nb = ci[rp[i]:rp[i + 1]]
             nb = nb[nb != i]
             assert not np.any(col[nb] == col[i])
-            higher = nb[prio[nb] > prio[i]]
+            higher = nb[(prio[nb] > prio[i]) | ((prio[nb] == prio[i]) & (nb < i))]
             used = set(col[higher].tolist())
             smallest = next(c for c in range(len(used) + 1) if c not in used)
             assert col[i] == smallest
+
+
+def test_coarse_levels_use_3_to_the_d_colours(oracle_mod):
+    """Jittered meshes give radius-2 Galerkin stencils on the uniform coarse
+    levels; the class-first priority then colours them with exactly 3^d colours
+    (a 3^d block of lattice points is a clique, so this is optimal)."""
+    for dim, n in [(2, 65), (3, 17)]:
+        p = _prob(dim, n, 1)
+        o = oracle_mod.Oracle(p)
+        checked = 0
+        for l in range(2, o.num_levels):
+            nv, _, ncol = o.level_info(l)
+            if nv >= 7 ** dim:
+                assert ncol == 3 ** dim, (dim, l, ncol)
+                checked += 1
+        assert checked >= 1
 
 
 @pytest.mark.parametrize("dim,n,seed", [(2, 8, 3), (3, 4, 4)])

@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every kernel from the host instead of one CUDA graph per solve")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="time the solves only (no per-kernel roofline timing, e2e, FP64 path or CPU "
+                         "baseline); used for profiler launch lists")
     return ap.parse_args()
 
 
@@ -182,7 +187,7 @@ def ours(args):
     nfree = n - prob["dirichlet_dofs"].size
 
     def run_solver(precision):
-        s = vasmg.Solver(prob, precision=precision, stream=stream)
+        s = vasmg.Solver(prob, precision=precision, stream=stream, use_graph=not args.no_graph)
         F = torch.zeros(n, dtype=torch.float64, device=dev)
         s.assemble_load(prob["body_force"], F)
         U = torch.zeros_like(F)
@@ -220,6 +225,14 @@ def ours(args):
     clk = clocks.stop()
     work = nfree * sum(iters) * world
     value = work / (ms / 1e3) / 1e6
+    if args.solve_only:
+        if rank == 0:
+            print(json.dumps({"metric": "V-ASMG-PCG MDOF*iter/s to 1e-6 rel. residual", "value": value,
+                              "unit": "MDOF*iter/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": ms / args.steps, "iterations": iters[0], "gpu_launches": launches,
+                              "graph": not args.no_graph, "solve_only": True, "clocks": clk}), flush=True)
+        s.close()
+        return
     # roofline: every launch class of one iteration timed alone on the library's
     # stream (CUDA events); the dominant one is reported
     peaks, peak_src = load_peaks()

@@ -96,6 +96,15 @@ __device__ __forceinline__ int ld_acquire_i(const int* p) {
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // ------------------------------------------------------------------ level view
 
@@ -185,6 +194,93 @@ __device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int 
   }
 }
 
+// Entries a lane keeps in registers between the prefetch and the finish of a row.
+template <int D, typename V>
+struct RowPF {
+  static constexpr int NPF = (D * D * sizeof(V) <= 16) ? 2 : 1;
+  int k0, k1;
+  int cj[NPF];
+  V a[NPF][D * D];
+  V di[D], bv[D];
+};
+
+// Row pass split in two.  row_prefetch loads everything that no other tile
+// writes during the launch (row range, the first NPF entries of this lane,
+// the diagonal inverse and b); row_finish, called once the tiles this row
+// depends on are done, gathers x and completes the row as row_pass does.
+template <int D, int G, typename V, typename S, int MODE, typename L_t>
+__device__ __forceinline__ void row_prefetch(const L_t& L, int row, bool valid, int lane, RowPF<D, V>& st) {
+  constexpr int NPF = RowPF<D, V>::NPF;
+  st.k0 = 0;
+  st.k1 = 0;
+  if (valid) {
+    st.k0 = MODE == 2 ? __ldg(L.sp + row) : __ldg(L.rp + row);
+    st.k1 = MODE == 0 ? __ldg(L.sp + row) : __ldg(L.rp + row + 1);
+  }
+  const S* off = (const S*)L.off;
+#pragma unroll
+  for (int p = 0; p < NPF; ++p) {
+    const int k = st.k0 + lane + p * G;
+    st.cj[p] = -1;
+    if (k < st.k1) {
+      st.cj[p] = __ldg(L.ci + k);
+#pragma unroll
+      for (int q = 0; q < D * D; ++q) st.a[p][q] = ldv<V, S>(off + (long long)q * L.nnz + k);
+    }
+  }
+  if (MODE != 2 && valid && lane < D) {
+#pragma unroll
+    for (int bb = 0; bb < D; ++bb) {
+      st.di[bb] = __ldg((const V*)L.dinv + (long long)(lane * D + bb) * L.nv + row);
+      st.bv[bb] = ldx((const V*)L.b + (long long)row * D + bb);
+    }
+  }
+}
+
+template <int D, int G, typename V, typename S, int MODE, typename L_t>
+__device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, int lane, const RowPF<D, V>& st) {
+  constexpr int NPF = RowPF<D, V>::NPF;
+  V acc[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) acc[a] = V(0);
+#pragma unroll
+  for (int p = 0; p < NPF; ++p) {
+    if (st.cj[p] >= 0) {
+      V xj[D];
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb) xj[bb] = ldx(L.x + (long long)st.cj[p] * D + bb);
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int bb = 0; bb < D; ++bb) acc[a] += st.a[p][a * D + bb] * xj[bb];
+    }
+  }
+  const S* off = (const S*)L.off;
+  for (int k = st.k0 + lane + NPF * G; k < st.k1; k += G) {
+    const int j = __ldg(L.ci + k);
+    V xj[D];
+#pragma unroll
+    for (int bb = 0; bb < D; ++bb) xj[bb] = ldx(L.x + (long long)j * D + bb);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb) acc[a] += ldv<V, S>(off + (long long)(a * D + bb) * L.nnz + k) * xj[bb];
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o, G);
+  if (!valid || lane >= D) return;
+  if (MODE == 2) {
+    stx(L.r + (long long)row * D + lane, -pick<D>(acc, lane));
+  } else {
+    V s = V(0);
+#pragma unroll
+    for (int bb = 0; bb < D; ++bb) s += st.di[bb] * (st.bv[bb] - acc[bb]);
+    stx(L.x + (long long)row * D + lane, s);
+  }
+}
+
 template <int D, typename V, typename L_t>
 __device__ __forceinline__ void restrict_row(const L_t& L, int I) {
   V acc[D];
@@ -232,15 +328,18 @@ __device__ __forceinline__ bool wait_tiles(const int* __restrict__ list, int n, 
     for (int k = threadIdx.x; k < n && ok; k += 32) {
       const unsigned* f = flags + __ldg(list + k);
       int spins = 0;
-      while (ld_acquire(f) != epoch) {
+      unsigned ns = 32;
+      while (ld_relaxed(f) != epoch) {
         if (++spins > SPIN_LIMIT || *(volatile int*)abort_flag) {
           atomicExch(abort_flag, 1);
           ok = false;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(ns);
+        ns = ns < 256 ? 2 * ns : 256;
       }
     }
+    fence_acq_rel();  // acquire every flag read above
     ok = __all_sync(0xffffffffu, ok);
     if (threadIdx.x == 0) s_ok = ok ? 1 : 0;
   }
@@ -266,16 +365,16 @@ __device__ __forceinline__ bool wait_count(const int* ctr, int target, int* abor
   return s_ok != 0;
 }
 
-// Make this tile's writes visible at GPU scope, then stamp its flag.
+// Stamp this tile's flag once every thread of the block has written: the
+// barrier orders the block's writes before thread 0's release, and a release
+// is cumulative, so a reader that acquires the flag sees all of them.
 __device__ __forceinline__ void publish_tile(unsigned* flag, unsigned epoch) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) st_release(flag, epoch);
 }
 __device__ __forceinline__ void publish_count(int* ctr) {
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(ctr, 1);
+  if (threadIdx.x == 0) red_release_add(ctr, 1);
 }
 
 // Claim the next work item; also broadcasts the abort flag.
@@ -304,12 +403,52 @@ __device__ __forceinline__ void leave(int* ctr, int claim_i, int exit_i, int don
 }
 
 // ------------------------------------------------------------------ down / up launches
+//
+// Items are claimed one ahead: thread 0 issues the atomic for the next item
+// when it starts the current one, and hands the result over through a
+// parity-indexed shared slot at the item's closing barrier.  Claims stay in
+// increasing order, so the smallest unfinished item is always some CTA's
+// current item and can proceed.
+
+// Minimum resident CTAs per SM the kernels are compiled for (register cap).
+template <int D, typename V>
+constexpr int df_min_blocks() { return (D == 2 && sizeof(V) == 4) ? 3 : 2; }
+
+// One sweep tile: prefetch both passes of rows, wait, finish.
+template <int D, int G, typename V, typename S, int MODE>
+__device__ __forceinline__ bool sweep_tile(const LV<V>& L, int tile, const int* dep_rp, const int* dep,
+                                           const unsigned* flags, unsigned epoch, int* abort_flag,
+                                           const int* count_ctr, int count_target) {
+  constexpr int NG = DF_THREADS / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  const int r0 = __ldg(L.ts + tile), r1 = __ldg(L.ts + tile + 1);
+  RowPF<D, V> st0, st1;
+  row_prefetch<D, G, V, S, MODE>(L, r0 + g, r0 + g < r1, lane, st0);
+  row_prefetch<D, G, V, S, MODE>(L, r0 + NG + g, r0 + NG + g < r1, lane, st1);
+  if (count_ctr && !wait_count(count_ctr, count_target, abort_flag)) return false;
+  const int b0 = __ldg(dep_rp + tile), b1 = __ldg(dep_rp + tile + 1);
+  if (!wait_tiles(dep + b0, b1 - b0, flags, epoch, abort_flag)) return false;
+  row_finish<D, G, V, S, MODE>(L, r0 + g, r0 + g < r1, lane, st0);
+  row_finish<D, G, V, S, MODE>(L, r0 + NG + g, r0 + NG + g < r1, lane, st1);
+  for (int base = r0 + 2 * NG; base < r1; base += NG)  // tiles never exceed two passes; kept for safety
+    row_pass<D, G, V, S, MODE>(L, base + g, base + g < r1, lane);
+  return true;
+}
+
+__device__ __forceinline__ int claim_issue(int* ctr, const int* abort_flag) {
+  return *(volatile const int*)abort_flag ? INT32_MAX : atomicAdd(ctr, 1);
+}
 
 // phases: 1 forward sweep (zero start), 2 residual, 4 restriction
 template <int D, int G, typename V, typename S>
-__global__ void __launch_bounds__(DF_THREADS) vdown_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
+__global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
+    vdown_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
   __shared__ unsigned s_epoch;
-  if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_DEPOCH);
+  __shared__ int s_next[2];
+  if (threadIdx.x == 0) {
+    s_epoch = *(volatile unsigned*)(L.ctr + C_DEPOCH);
+    s_next[0] = claim_issue(L.ctr + C_DCLAIM, &sc->abort);
+  }
   __syncthreads();
   const unsigned epoch = s_epoch;
   const int T = L.T;
@@ -317,63 +456,71 @@ __global__ void __launch_bounds__(DF_THREADS) vdown_kernel(const __grid_constant
   const int nres = (phases & 2) ? T : 0;
   const int nrc = (phases & 4) ? (L.nvc + RC_ROWS - 1) / RC_ROWS : 0;
   const int total = nsw + nres + nrc;
-  constexpr int NG = DF_THREADS / G;
-  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
-  for (;;) {
-    const int t = claim(L.ctr + C_DCLAIM, &sc->abort);
-    if (t >= total) break;
+  int* abort_flag = &sc->abort;
+  int t = s_next[0];
+  for (int it = 1; t < total; ++it) {
+    int nt = 0;
+    if (threadIdx.x == 0) nt = claim_issue(L.ctr + C_DCLAIM, abort_flag);
     if (t < nsw) {
-      const int b0 = __ldg(L.dlo_rp + t), b1 = __ldg(L.dlo_rp + t + 1);
-      if (!wait_tiles(L.dlo + b0, b1 - b0, L.fl_down, epoch, &sc->abort)) break;
-      const int r0 = __ldg(L.ts + t), r1 = __ldg(L.ts + t + 1);
-      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 0>(L, base + g, base + g < r1, lane);
-      publish_tile(L.fl_down + t, epoch);
+      if (!sweep_tile<D, G, V, S, 0>(L, t, L.dlo_rp, L.dlo, L.fl_down, epoch, abort_flag, nullptr, 0)) break;
+      if (threadIdx.x == 0) s_next[it & 1] = nt;
+      __syncthreads();
+      if (threadIdx.x == 0) st_release(L.fl_down + t, epoch);
     } else if (t < nsw + nres) {
-      const int tt = t - nsw;
-      const int b0 = __ldg(L.dhi_rp + tt), b1 = __ldg(L.dhi_rp + tt + 1);
-      if (!wait_tiles(L.dhi + b0, b1 - b0, L.fl_down, epoch, &sc->abort)) break;
-      const int r0 = __ldg(L.ts + tt), r1 = __ldg(L.ts + tt + 1);
-      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 2>(L, base + g, base + g < r1, lane);
-      publish_count(L.ctr + C_RESDONE);
+      if (!sweep_tile<D, G, V, S, 2>(L, t - nsw, L.dhi_rp, L.dhi, L.fl_down, epoch, abort_flag, nullptr, 0)) break;
+      if (threadIdx.x == 0) s_next[it & 1] = nt;
+      __syncthreads();
+      if (threadIdx.x == 0) red_release_add(L.ctr + C_RESDONE, 1);
     } else {
       const int tc = t - nsw - nres;
-      if (nres && !wait_count(L.ctr + C_RESDONE, T, &sc->abort)) break;
+      if (nres && !wait_count(L.ctr + C_RESDONE, T, abort_flag)) break;
       const int I = tc * RC_ROWS + (int)threadIdx.x;
       if (threadIdx.x < RC_ROWS && I < L.nvc) restrict_row<D, V>(L, I);
+      if (threadIdx.x == 0) s_next[it & 1] = nt;
+      __syncthreads();
     }
+    t = s_next[it & 1];
   }
   leave(L.ctr, C_DCLAIM, C_DEXIT, C_RESDONE, C_DEPOCH);
 }
 
 // phases: 1 prolongation + correction, 2 backward sweep
 template <int D, int G, typename V, typename S>
-__global__ void __launch_bounds__(DF_THREADS) vup_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
+__global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
+    vup_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
   __shared__ unsigned s_epoch;
-  if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_UEPOCH);
+  __shared__ int s_next[2];
+  if (threadIdx.x == 0) {
+    s_epoch = *(volatile unsigned*)(L.ctr + C_UEPOCH);
+    s_next[0] = claim_issue(L.ctr + C_UCLAIM, &sc->abort);
+  }
   __syncthreads();
   const unsigned epoch = s_epoch;
   const int T = L.T;
   const int npr = (phases & 1) ? (L.nv + RP_ROWS - 1) / RP_ROWS : 0;
   const int nsw = (phases & 2) ? T : 0;
   const int total = npr + nsw;
-  constexpr int NG = DF_THREADS / G;
-  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
-  for (;;) {
-    const int t = claim(L.ctr + C_UCLAIM, &sc->abort);
-    if (t >= total) break;
+  int* abort_flag = &sc->abort;
+  int t = s_next[0];
+  for (int it = 1; t < total; ++it) {
+    int nt = 0;
+    if (threadIdx.x == 0) nt = claim_issue(L.ctr + C_UCLAIM, abort_flag);
     if (t < npr) {
       const int i = t * RP_ROWS + (int)threadIdx.x;
       if (threadIdx.x < RP_ROWS && i < L.nv) prolong_row<D, V>(L, i);
-      publish_count(L.ctr + C_PRODONE);
+      if (threadIdx.x == 0) s_next[it & 1] = nt;
+      __syncthreads();
+      if (threadIdx.x == 0) red_release_add(L.ctr + C_PRODONE, 1);
     } else {
       const int tile = T - 1 - (t - npr);  // colours in reverse order
-      if (npr && !wait_count(L.ctr + C_PRODONE, npr, &sc->abort)) break;
-      const int b0 = __ldg(L.dhi_rp + tile), b1 = __ldg(L.dhi_rp + tile + 1);
-      if (!wait_tiles(L.dhi + b0, b1 - b0, L.fl_up, epoch, &sc->abort)) break;
-      const int r0 = __ldg(L.ts + tile), r1 = __ldg(L.ts + tile + 1);
-      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 1>(L, base + g, base + g < r1, lane);
-      publish_tile(L.fl_up + tile, epoch);
+      if (!sweep_tile<D, G, V, S, 1>(L, tile, L.dhi_rp, L.dhi, L.fl_up, epoch, abort_flag,
+                                     npr ? L.ctr + C_PRODONE : nullptr, npr))
+        break;
+      if (threadIdx.x == 0) s_next[it & 1] = nt;
+      __syncthreads();
+      if (threadIdx.x == 0) st_release(L.fl_up + tile, epoch);
     }
+    t = s_next[it & 1];
   }
   leave(L.ctr, C_UCLAIM, C_UEXIT, C_PRODONE, C_UEPOCH);
 }
@@ -576,13 +723,18 @@ __device__ __forceinline__ bool last_block_sum(double v, double* part, unsigned 
   return true;
 }
 
+// COND: the kernel runs inside the WHILE graph and sets its condition.  The
+// variants without it are the ones a profiler can replay.
+template <bool COND>
 __device__ __forceinline__ void set_cond(unsigned long long h, unsigned int v) {
-  if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
+  if constexpr (COND) {
+    if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
+  }
 }
 
 // r = F - A u_D at free dofs (0 at Dirichlet dofs), gathered into solve order;
 // U = p = 0; res0 = ||r||; b_0 = (V) r.
-template <int D, typename V>
+template <int D, typename V, bool COND>
 __global__ void __launch_bounds__(CG_THREADS) cg_init_kernel(CGArgs a, const double* __restrict__ F, V* b0) {
   double acc = 0.0;
   const long long n = (long long)a.nv * D;
@@ -610,12 +762,12 @@ __global__ void __launch_bounds__(CG_THREADS) cg_init_kernel(CGArgs a, const dou
     s->abort = 0;
     s->done = (s->res0 == 0.0) ? 1 : 0;
     if (s->done) s->relres = 0.0;
-    set_cond(a.cond, s->done ? 0u : 1u);
+    set_cond<COND>(a.cond, s->done ? 0u : 1u);
   }
 }
 
 // rho_new = r . z; beta = rho_new / rho (0 on the first iteration)
-template <int D, typename V>
+template <int D, typename V, bool COND>
 __global__ void __launch_bounds__(CG_THREADS) rz_kernel(CGArgs a, const V* __restrict__ z) {
   double acc = 0.0;
   const long long n = (long long)a.nv * D;
@@ -629,7 +781,7 @@ __global__ void __launch_bounds__(CG_THREADS) rz_kernel(CGArgs a, const V* __res
     if (s->bodies > s->max_iters + 2) {
       s->done = 1;
       s->status = VASMG_ERR_TIMEOUT;
-      set_cond(a.cond, 0u);
+      set_cond<COND>(a.cond, 0u);
     }
   }
   double tot;
@@ -650,7 +802,7 @@ __global__ void __launch_bounds__(CG_THREADS) p_update_kernel(CGArgs a, const V*
 }
 
 // q = A p (SELL-32, one thread per row, one warp per slice), p.q, alpha.
-template <int D>
+template <int D, bool COND>
 __global__ void __launch_bounds__(CG_THREADS) spmv_sell_kernel(CGArgs a, int with_dot) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -693,7 +845,7 @@ __global__ void __launch_bounds__(CG_THREADS) spmv_sell_kernel(CGArgs a, int wit
       s->status = VASMG_ERR_BREAKDOWN;
       s->done = 1;
       s->alpha = 0.0;
-      set_cond(a.cond, 0u);
+      set_cond<COND>(a.cond, 0u);
     } else {
       s->alpha = s->rho / tot;
     }
@@ -701,7 +853,7 @@ __global__ void __launch_bounds__(CG_THREADS) spmv_sell_kernel(CGArgs a, int wit
 }
 
 // U += alpha p; r -= alpha q; ||r||; stop test; b_0 = (V) r.
-template <int D, typename V>
+template <int D, typename V, bool COND>
 __global__ void __launch_bounds__(CG_THREADS) cg_update_kernel(CGArgs a, V* b0) {
   if (a.sc->done) return;  // breakdown in spmv
   const double alpha = a.sc->alpha;
@@ -735,7 +887,7 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update_kernel(CGArgs a, V* b0) 
       s->status = VASMG_NOT_CONVERGED;
     }
     if (s->bodies > s->max_iters + 2) s->done = 1;
-    set_cond(a.cond, s->done ? 0u : 1u);
+    set_cond<COND>(a.cond, s->done ? 0u : 1u);
   }
 }
 
@@ -1280,7 +1432,10 @@ struct Engine : EngineBase {
   }
 
   void spmv(cudaStream_t s, int with_dot) {
-    spmv_sell_kernel<D><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot);
+    if (cga.cond)
+      spmv_sell_kernel<D, true><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot);
+    else
+      spmv_sell_kernel<D, false><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot);
     ++launch_counter;
   }
 
@@ -1289,10 +1444,16 @@ struct Engine : EngineBase {
   void body(cudaStream_t s) {
     V* z = lv[0].x;
     vcycle(0, s);
-    rz_kernel<D, V><<<cg_blocks, CG_THREADS, 0, s>>>(cga, z);
+    if (cga.cond)
+      rz_kernel<D, V, true><<<cg_blocks, CG_THREADS, 0, s>>>(cga, z);
+    else
+      rz_kernel<D, V, false><<<cg_blocks, CG_THREADS, 0, s>>>(cga, z);
     p_update_kernel<D, V><<<cg_blocks, CG_THREADS, 0, s>>>(cga, z);
     spmv(s, 1);
-    cg_update_kernel<D, V><<<cg_blocks, CG_THREADS, 0, s>>>(cga, lv[0].b);
+    if (cga.cond)
+      cg_update_kernel<D, V, true><<<cg_blocks, CG_THREADS, 0, s>>>(cga, lv[0].b);
+    else
+      cg_update_kernel<D, V, false><<<cg_blocks, CG_THREADS, 0, s>>>(cga, lv[0].b);
     launch_counter += 3;
   }
 
@@ -1310,7 +1471,7 @@ struct Engine : EngineBase {
       cga.cond = (unsigned long long)h;
       ok = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       if (ok) {
-        cg_init_kernel<D, V><<<cg_blocks, CG_THREADS, 0, s>>>(cga, Fbuf.get(), lv[0].b);
+        cg_init_kernel<D, V, true><<<cg_blocks, CG_THREADS, 0, s>>>(cga, Fbuf.get(), lv[0].b);
         ok = cudaStreamEndCapture(s, &out) == cudaSuccess;
       }
     }
@@ -1387,7 +1548,7 @@ struct Engine : EngineBase {
       VASMG_CUDA(cudaMemcpyAsync(host_sc, sc.get(), sizeof(Scalars), cudaMemcpyDeviceToHost, s));
       VASMG_CUDA(cudaStreamSynchronize(s));
     } else {
-      cg_init_kernel<D, V><<<cg_blocks, CG_THREADS, 0, s>>>(cga, Fbuf.get(), lv[0].b);
+      cg_init_kernel<D, V, false><<<cg_blocks, CG_THREADS, 0, s>>>(cga, Fbuf.get(), lv[0].b);
       check_launch("cg_init");
       VASMG_CUDA(cudaMemcpyAsync(host_sc, sc.get(), sizeof(Scalars), cudaMemcpyDeviceToHost, s));
       VASMG_CUDA(cudaStreamSynchronize(s));

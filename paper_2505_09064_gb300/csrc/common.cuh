@@ -153,6 +153,7 @@ struct SolveLevel {
   i64 nv = 0, nnz = 0;
   int ncol = 0;
   std::vector<int32_t> cs;      // host copy of colour starts [ncol+1]
+  std::vector<uint32_t> sec;    // host: spatial key of each solve row (ascending within a colour)
   DevBuf<int32_t> perm, iperm;  // solve index -> canonical, canonical -> solve
   DevBuf<int32_t> rp, ci, sp;   // sp[i]: first entry of row i whose column is of a later colour
   DevBuf<double> off64;         // [d*d][nnz]

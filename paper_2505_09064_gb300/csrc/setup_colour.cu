@@ -391,6 +391,8 @@ void setup_colour_and_solve_levels(Ctx& c) {
       invert_perm_kernel<<<grid_for(cl.nv, 256), 256, 0, s>>>(sl.perm.get(), cl.nv, sl.iperm.get());
       check_launch("invert_perm");
       std::vector<u64> hk = keys.download();
+      sl.sec.resize(hk.size());
+      for (size_t i = 0; i < hk.size(); ++i) sl.sec[i] = (uint32_t)hk[i];
       sl.cs.assign(cl.ncol + 1, 0);
       for (int col = 0; col <= cl.ncol; ++col) {
         const u64 t = (u64)col << 32;

@@ -50,8 +50,7 @@ constexpr int TAIL_G = 8;
 constexpr int MAX_LEVELS = 40;
 constexpr int CG_THREADS = 256;
 constexpr int DF_THREADS = 256;
-constexpr int RC_ROWS = 256;      // coarse rows per restriction tile
-constexpr int RP_ROWS = 256;      // fine rows per prolongation tile
+constexpr int REGION_MIN_ROWS = 32;  // fewest rows a sweep region is given
 constexpr int SPIN_LIMIT = 1 << 20;   // ~0.1-0.5 s of polling before a wait gives up
 
 struct Scalars {
@@ -60,9 +59,8 @@ struct Scalars {
   unsigned int cnt[4];
 };
 
-// per-level launch state: [0] down claim [1] down exit [2] residual tiles done
-// [3] down epoch [4] up claim [5] up exit [6] prolongation tiles done [7] up epoch
-enum { C_DCLAIM = 0, C_DEXIT, C_RESDONE, C_DEPOCH, C_UCLAIM, C_UEXIT, C_PRODONE, C_UEPOCH, C_N };
+// per-level launch state: exit counters and epochs of the down and up launches
+enum { C_DEXIT = 0, C_DEPOCH, C_UEXIT, C_UEPOCH, C_N };
 
 // ------------------------------------------------------------------ memory helpers
 
@@ -105,6 +103,14 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
   return v;
 }
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 // ------------------------------------------------------------------ level view
 
@@ -132,15 +138,16 @@ struct LV {
   const V* rw;
   V* bc;                  // b of level l+1
   const V* xc;            // x of level l+1
-  // self-scheduling state
-  int T;                  // sweep tiles
-  const int* ts;          // tile row starts [T+1]
-  const int* dlo_rp;      // tiles of earlier colours holding neighbours
-  const int* dlo;
-  const int* dhi_rp;      // tiles of later colours holding neighbours
-  const int* dhi;
-  unsigned* fl_down;
-  unsigned* fl_up;
+  // region decomposition: CTA k of a sweep launch owns region k, the rows
+  // whose spatial key lies in the k-th of R equal key ranges
+  int R;
+  const int* RS;          // [ncol][R+1]: rows of colour c in region k = [RS[c][k], RS[c][k+1])
+  const int* nb_rp;       // regions holding a neighbour of a row of region k (CSR, k excluded)
+  const int* nb;
+  const int* rd_rp;       // regions holding a fine row that a coarse row of region k restricts
+  const int* rd;
+  unsigned long long* pg_d;  // progress of each region in the down launch: epoch << 32 | stage
+  unsigned long long* pg_u;  // same for the up launch
   int* ctr;               // C_N counters
 };
 
@@ -316,20 +323,23 @@ __device__ __forceinline__ void prolong_row(const L_t& L, int i) {
     }
 }
 
-// ------------------------------------------------------------------ self-scheduling helpers
+// ------------------------------------------------------------------ region progress
 
-// Wait until every tile in list[0..n) carries `epoch` (warp 0 polls); returns
-// false (uniformly) if a wait gave up or the abort flag is up.
-__device__ __forceinline__ bool wait_tiles(const int* __restrict__ list, int n, const unsigned* flags,
-                                           unsigned epoch, int* abort_flag) {
+// Wait until every region in list[0..n) has published stage >= need in this
+// launch (epoch); false (uniform over the CTA) if a wait gave up or the abort
+// flag is up.  Warp 0 polls relaxed loads with back-off, then acquires once.
+__device__ __forceinline__ bool wait_regions(const int* __restrict__ list, int n, const unsigned long long* pg,
+                                             unsigned epoch, unsigned need, int* abort_flag) {
   __shared__ int s_ok;
   if (threadIdx.x < 32) {
     bool ok = true;
     for (int k = threadIdx.x; k < n && ok; k += 32) {
-      const unsigned* f = flags + __ldg(list + k);
+      const unsigned long long* f = pg + __ldg(list + k);
       int spins = 0;
       unsigned ns = 32;
-      while (ld_relaxed(f) != epoch) {
+      for (;;) {
+        const unsigned long long v = ld_relaxed64(f);
+        if ((unsigned)(v >> 32) == epoch && (unsigned)v >= need) break;
         if (++spins > SPIN_LIMIT || *(volatile int*)abort_flag) {
           atomicExch(abort_flag, 1);
           ok = false;
@@ -339,7 +349,7 @@ __device__ __forceinline__ bool wait_tiles(const int* __restrict__ list, int n, 
         ns = ns < 256 ? 2 * ns : 256;
       }
     }
-    fence_acq_rel();  // acquire every flag read above
+    fence_acq_rel();
     ok = __all_sync(0xffffffffu, ok);
     if (threadIdx.x == 0) s_ok = ok ? 1 : 0;
   }
@@ -347,54 +357,20 @@ __device__ __forceinline__ bool wait_tiles(const int* __restrict__ list, int n, 
   return s_ok != 0;
 }
 
-__device__ __forceinline__ bool wait_count(const int* ctr, int target, int* abort_flag) {
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    int ok = 1, spins = 0;
-    while (ld_acquire_i(ctr) < target) {
-      if (++spins > SPIN_LIMIT || *(volatile int*)abort_flag) {
-        atomicExch(abort_flag, 1);
-        ok = 0;
-        break;
-      }
-      __nanosleep(32);
-    }
-    s_ok = ok;
-  }
+// Publish this region's stage once every thread of the CTA has written: the
+// barrier orders the CTA's writes before thread 0's release, and a release
+// is cumulative, so a CTA that acquires the stage sees all of them.
+__device__ __forceinline__ void publish_stage(unsigned long long* f, unsigned epoch, unsigned stage) {
   __syncthreads();
-  return s_ok != 0;
+  if (threadIdx.x == 0) st_release64(f, ((unsigned long long)epoch << 32) | stage);
 }
 
-// Stamp this tile's flag once every thread of the block has written: the
-// barrier orders the block's writes before thread 0's release, and a release
-// is cumulative, so a reader that acquires the flag sees all of them.
-__device__ __forceinline__ void publish_tile(unsigned* flag, unsigned epoch) {
-  __syncthreads();
-  if (threadIdx.x == 0) st_release(flag, epoch);
-}
-__device__ __forceinline__ void publish_count(int* ctr) {
-  __syncthreads();
-  if (threadIdx.x == 0) red_release_add(ctr, 1);
-}
-
-// Claim the next work item; also broadcasts the abort flag.
-__device__ __forceinline__ int claim(int* ctr, const int* abort_flag) {
-  __shared__ int s_t;
-  __syncthreads();
-  if (threadIdx.x == 0) s_t = *(volatile const int*)abort_flag ? INT32_MAX : atomicAdd(ctr, 1);
-  __syncthreads();
-  return s_t;
-}
-
-// The last block to leave resets the launch's counters and advances its epoch.
-__device__ __forceinline__ void leave(int* ctr, int claim_i, int exit_i, int done_i, int epoch_i) {
+// The last CTA to leave advances the launch's epoch.
+__device__ __forceinline__ void leave(int* ctr, int exit_i, int epoch_i) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    const int e = atomicAdd(ctr + exit_i, 1);
-    if (e == (int)gridDim.x - 1) {
-      ctr[claim_i] = 0;
-      ctr[done_i] = 0;
+    if (atomicAdd(ctr + exit_i, 1) == (int)gridDim.x - 1) {
       ctr[exit_i] = 0;
       ctr[epoch_i] += 1;
       __threadfence();
@@ -402,86 +378,88 @@ __device__ __forceinline__ void leave(int* ctr, int claim_i, int exit_i, int don
   }
 }
 
+// Rows [r0, r1) of one colour, NG rows per pass; the next pass's entries are
+// loaded while the current pass gathers x.  `cur` holds the first pass.
+template <int D, int G, typename V, typename S, int MODE>
+__device__ __forceinline__ void rows_pipelined(const LV<V>& L, int r0, int r1, RowPF<D, V>& cur) {
+  constexpr int NG = DF_THREADS / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  for (int base = r0; base < r1; base += NG) {
+    const int nb = base + NG;
+    RowPF<D, V> nxt;
+    if (nb < r1) row_prefetch<D, G, V, S, MODE>(L, nb + g, nb + g < r1, lane, nxt);
+    row_finish<D, G, V, S, MODE>(L, base + g, base + g < r1, lane, cur);
+    if (nb < r1) cur = nxt;
+  }
+}
+
 // ------------------------------------------------------------------ down / up launches
 //
-// Items are claimed one ahead: thread 0 issues the atomic for the next item
-// when it starts the current one, and hands the result over through a
-// parity-indexed shared slot at the item's closing barrier.  Claims stay in
-// increasing order, so the smallest unfinished item is always some CTA's
-// current item and can proceed.
+// One cooperative launch per level and direction, CTA k = region k.  A
+// region runs its rows colour by colour; before colour c it waits until every
+// neighbouring region has finished the colours it reads (forward: all
+// earlier colours; backward: all later colours and the prolongation).  The
+// neighbour relation is symmetric, so the same waits also keep a region from
+// overwriting values a neighbour has still to read.
 
 // Minimum resident CTAs per SM the kernels are compiled for (register cap).
 template <int D, typename V>
 constexpr int df_min_blocks() { return (D == 2 && sizeof(V) == 4) ? 3 : 2; }
-
-// One sweep tile: prefetch both passes of rows, wait, finish.
-template <int D, int G, typename V, typename S, int MODE>
-__device__ __forceinline__ bool sweep_tile(const LV<V>& L, int tile, const int* dep_rp, const int* dep,
-                                           const unsigned* flags, unsigned epoch, int* abort_flag,
-                                           const int* count_ctr, int count_target) {
-  constexpr int NG = DF_THREADS / G;
-  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
-  const int r0 = __ldg(L.ts + tile), r1 = __ldg(L.ts + tile + 1);
-  RowPF<D, V> st0, st1;
-  row_prefetch<D, G, V, S, MODE>(L, r0 + g, r0 + g < r1, lane, st0);
-  row_prefetch<D, G, V, S, MODE>(L, r0 + NG + g, r0 + NG + g < r1, lane, st1);
-  if (count_ctr && !wait_count(count_ctr, count_target, abort_flag)) return false;
-  const int b0 = __ldg(dep_rp + tile), b1 = __ldg(dep_rp + tile + 1);
-  if (!wait_tiles(dep + b0, b1 - b0, flags, epoch, abort_flag)) return false;
-  row_finish<D, G, V, S, MODE>(L, r0 + g, r0 + g < r1, lane, st0);
-  row_finish<D, G, V, S, MODE>(L, r0 + NG + g, r0 + NG + g < r1, lane, st1);
-  for (int base = r0 + 2 * NG; base < r1; base += NG)  // tiles never exceed two passes; kept for safety
-    row_pass<D, G, V, S, MODE>(L, base + g, base + g < r1, lane);
-  return true;
-}
-
-__device__ __forceinline__ int claim_issue(int* ctr, const int* abort_flag) {
-  return *(volatile const int*)abort_flag ? INT32_MAX : atomicAdd(ctr, 1);
-}
 
 // phases: 1 forward sweep (zero start), 2 residual, 4 restriction
 template <int D, int G, typename V, typename S>
 __global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
     vdown_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
   __shared__ unsigned s_epoch;
-  __shared__ int s_next[2];
-  if (threadIdx.x == 0) {
-    s_epoch = *(volatile unsigned*)(L.ctr + C_DEPOCH);
-    s_next[0] = claim_issue(L.ctr + C_DCLAIM, &sc->abort);
-  }
+  if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_DEPOCH);
   __syncthreads();
   const unsigned epoch = s_epoch;
-  const int T = L.T;
-  const int nsw = (phases & 1) ? T : 0;
-  const int nres = (phases & 2) ? T : 0;
-  const int nrc = (phases & 4) ? (L.nvc + RC_ROWS - 1) / RC_ROWS : 0;
-  const int total = nsw + nres + nrc;
+  const int k = blockIdx.x, R = L.R, C = L.ncol;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  const int nb0 = __ldg(L.nb_rp + k), nnb = __ldg(L.nb_rp + k + 1) - nb0;
   int* abort_flag = &sc->abort;
-  int t = s_next[0];
-  for (int it = 1; t < total; ++it) {
-    int nt = 0;
-    if (threadIdx.x == 0) nt = claim_issue(L.ctr + C_DCLAIM, abort_flag);
-    if (t < nsw) {
-      if (!sweep_tile<D, G, V, S, 0>(L, t, L.dlo_rp, L.dlo, L.fl_down, epoch, abort_flag, nullptr, 0)) break;
-      if (threadIdx.x == 0) s_next[it & 1] = nt;
-      __syncthreads();
-      if (threadIdx.x == 0) st_release(L.fl_down + t, epoch);
-    } else if (t < nsw + nres) {
-      if (!sweep_tile<D, G, V, S, 2>(L, t - nsw, L.dhi_rp, L.dhi, L.fl_down, epoch, abort_flag, nullptr, 0)) break;
-      if (threadIdx.x == 0) s_next[it & 1] = nt;
-      __syncthreads();
-      if (threadIdx.x == 0) red_release_add(L.ctr + C_RESDONE, 1);
-    } else {
-      const int tc = t - nsw - nres;
-      if (nres && !wait_count(L.ctr + C_RESDONE, T, abort_flag)) break;
-      const int I = tc * RC_ROWS + (int)threadIdx.x;
-      if (threadIdx.x < RC_ROWS && I < L.nvc) restrict_row<D, V>(L, I);
-      if (threadIdx.x == 0) s_next[it & 1] = nt;
-      __syncthreads();
+  unsigned long long* mine = L.pg_d + k;
+  unsigned stage = 0;
+  bool ok = true;
+  if (phases & 1) {
+    for (int c = 0; c < C && ok; ++c) {
+      const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+      if (r0 < r1) {
+        RowPF<D, V> cur;
+        row_prefetch<D, G, V, S, 0>(L, r0 + g, r0 + g < r1, lane, cur);
+        if (c > 0 && !wait_regions(L.nb + nb0, nnb, L.pg_d, epoch, (unsigned)c, abort_flag)) {
+          ok = false;
+          break;
+        }
+        rows_pipelined<D, G, V, S, 0>(L, r0, r1, cur);
+      }
+      publish_stage(mine, epoch, (unsigned)(c + 1));
     }
-    t = s_next[it & 1];
+    stage = (unsigned)C;
   }
-  leave(L.ctr, C_DCLAIM, C_DEXIT, C_RESDONE, C_DEPOCH);
+  if (ok && (phases & 2)) {
+    if (stage > 0 && !wait_regions(L.nb + nb0, nnb, L.pg_d, epoch, stage, abort_flag)) ok = false;
+    if (ok) {
+      for (int c = 0; c < C; ++c) {
+        const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+        if (r0 < r1) {
+          RowPF<D, V> cur;
+          row_prefetch<D, G, V, S, 2>(L, r0 + g, r0 + g < r1, lane, cur);
+          rows_pipelined<D, G, V, S, 2>(L, r0, r1, cur);
+        }
+      }
+      publish_stage(mine, epoch, ++stage);
+    }
+  }
+  if (ok && (phases & 4)) {
+    const int d0 = __ldg(L.rd_rp + k), nrd = __ldg(L.rd_rp + k + 1) - d0;
+    if (stage > 0 && !wait_regions(L.rd + d0, nrd, L.pg_d, epoch, stage, abort_flag)) ok = false;
+    if (ok) {
+      const int I0 = (int)((long long)k * L.nvc / R), I1 = (int)((long long)(k + 1) * L.nvc / R);
+      for (int I = I0 + (int)threadIdx.x; I < I1; I += blockDim.x) restrict_row<D, V>(L, I);
+    }
+  }
+  leave(L.ctr, C_DEXIT, C_DEPOCH);
 }
 
 // phases: 1 prolongation + correction, 2 backward sweep
@@ -489,40 +467,35 @@ template <int D, int G, typename V, typename S>
 __global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
     vup_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
   __shared__ unsigned s_epoch;
-  __shared__ int s_next[2];
-  if (threadIdx.x == 0) {
-    s_epoch = *(volatile unsigned*)(L.ctr + C_UEPOCH);
-    s_next[0] = claim_issue(L.ctr + C_UCLAIM, &sc->abort);
-  }
+  if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_UEPOCH);
   __syncthreads();
   const unsigned epoch = s_epoch;
-  const int T = L.T;
-  const int npr = (phases & 1) ? (L.nv + RP_ROWS - 1) / RP_ROWS : 0;
-  const int nsw = (phases & 2) ? T : 0;
-  const int total = npr + nsw;
+  const int k = blockIdx.x, R = L.R, C = L.ncol;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  const int nb0 = __ldg(L.nb_rp + k), nnb = __ldg(L.nb_rp + k + 1) - nb0;
   int* abort_flag = &sc->abort;
-  int t = s_next[0];
-  for (int it = 1; t < total; ++it) {
-    int nt = 0;
-    if (threadIdx.x == 0) nt = claim_issue(L.ctr + C_UCLAIM, abort_flag);
-    if (t < npr) {
-      const int i = t * RP_ROWS + (int)threadIdx.x;
-      if (threadIdx.x < RP_ROWS && i < L.nv) prolong_row<D, V>(L, i);
-      if (threadIdx.x == 0) s_next[it & 1] = nt;
-      __syncthreads();
-      if (threadIdx.x == 0) red_release_add(L.ctr + C_PRODONE, 1);
-    } else {
-      const int tile = T - 1 - (t - npr);  // colours in reverse order
-      if (!sweep_tile<D, G, V, S, 1>(L, tile, L.dhi_rp, L.dhi, L.fl_up, epoch, abort_flag,
-                                     npr ? L.ctr + C_PRODONE : nullptr, npr))
-        break;
-      if (threadIdx.x == 0) s_next[it & 1] = nt;
-      __syncthreads();
-      if (threadIdx.x == 0) st_release(L.fl_up + tile, epoch);
+  unsigned long long* mine = L.pg_u + k;
+  unsigned stage = 0;
+  if (phases & 1) {
+    for (int c = 0; c < C; ++c) {
+      const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+      for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) prolong_row<D, V>(L, i);
     }
-    t = s_next[it & 1];
+    publish_stage(mine, epoch, ++stage);
   }
-  leave(L.ctr, C_UCLAIM, C_UEXIT, C_PRODONE, C_UEPOCH);
+  if (phases & 2) {
+    for (int c = C - 1; c >= 0; --c) {
+      const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+      if (r0 < r1) {
+        RowPF<D, V> cur;
+        row_prefetch<D, G, V, S, 1>(L, r0 + g, r0 + g < r1, lane, cur);
+        if (stage > 0 && !wait_regions(L.nb + nb0, nnb, L.pg_u, epoch, stage, abort_flag)) break;
+        rows_pipelined<D, G, V, S, 1>(L, r0, r1, cur);
+      }
+      publish_stage(mine, epoch, ++stage);
+    }
+  }
+  leave(L.ctr, C_UEXIT, C_UEPOCH);
 }
 
 // ------------------------------------------------------------------ coarsest solve and tail
@@ -905,31 +878,6 @@ __global__ void cg_final_kernel(CGArgs a, double* __restrict__ Uout) {
 
 // ------------------------------------------------------------------ setup kernels for the engine
 
-__global__ void row2tile_kernel(const int* __restrict__ ts, int T, int* __restrict__ row2tile) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
-    for (int r = ts[t]; r < ts[t + 1]; ++r) row2tile[r] = t;
-}
-
-// dependency pairs (tile << 32 | neighbour tile), lower and upper parts
-__global__ void dep_pairs_kernel(const int* __restrict__ rp, const int* __restrict__ sp, const int* __restrict__ ci,
-                                 const int* __restrict__ row2tile, int nv, const long long* __restrict__ lo_off,
-                                 const long long* __restrict__ hi_off, u64* __restrict__ lo, u64* __restrict__ hi) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
-    const u64 t = (u64)row2tile[r];
-    long long ol = lo_off[r], oh = hi_off[r];
-    for (int k = rp[r]; k < sp[r]; ++k) lo[ol++] = (t << 32) | (u64)row2tile[ci[k]];
-    for (int k = sp[r]; k < rp[r + 1]; ++k) hi[oh++] = (t << 32) | (u64)row2tile[ci[k]];
-  }
-}
-
-__global__ void split_counts_kernel(const int* __restrict__ rp, const int* __restrict__ sp, int nv,
-                                    long long* __restrict__ lo, long long* __restrict__ hi) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv; r += gridDim.x * blockDim.x) {
-    lo[r] = sp[r] - rp[r];
-    hi[r] = rp[r + 1] - sp[r];
-  }
-}
-
 __global__ void low32_e_kernel(const u64* __restrict__ k, i64 n, int* __restrict__ out) {
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     out[i] = (int)(k[i] & 0xffffffffull);
@@ -1029,11 +977,12 @@ struct EngineBase {
   virtual double time(Ctx& c, int which, int level, int reps, double* bytes) = 0;
 };
 
+// Lanes per row: few enough that a CTA pass covers many rows (the sweeps are
+// bound by the latency of their dependent loads, not by lane utilisation).
 static int pick_G(double avg) {
   if (avg <= 6.0) return 4;
-  if (avg <= 12.0) return 8;
-  if (avg <= 24.0) return 16;
-  return 32;
+  if (avg <= 48.0) return 8;
+  return 16;
 }
 
 template <int D, typename V, typename S>
@@ -1044,9 +993,8 @@ struct Engine : EngineBase {
   int nct = 1;     // CTAs in the tail cluster
   std::vector<LV<V>> lv;
   std::vector<int> G;
-  std::vector<DevBuf<int32_t>> cs_dev, ts_dev, dlo_rp, dlo, dhi_rp, dhi;
-  std::vector<DevBuf<unsigned>> fl_down, fl_up;
-  std::vector<int> grid_down, grid_up;
+  std::vector<DevBuf<int32_t>> cs_dev, rs_dev, nb_rp, nb, rd_rp, rd;
+  std::vector<DevBuf<unsigned long long>> pg_d, pg_u;
   DevBuf<int> ctrs;
   DevBuf<double> coarse_y;
   // CG
@@ -1091,64 +1039,79 @@ struct Engine : EngineBase {
     return (const V*)s.rw32.get();
   }
 
-  // tiles of one level: rows of a colour cut into pieces of two CTA passes
-  void build_tiles(int l) {
+  // Regions of one level.  The spatial keys (Morton rank of a fine vertex,
+  // lattice Morton order of a coarse one) are a permutation of 0..nv-1 and
+  // ascend within each colour, so region k (keys [k nv/R, (k+1) nv/R)) owns
+  // one contiguous row range per colour.
+  void build_regions(int l, int R) {
     cudaStream_t s = c->stream;
     SolveLevel& sl = c->S[l];
-    const int rows_per_tile = 2 * (DF_THREADS / G[l]);
-    std::vector<int> ts;
-    for (int col = 0; col < sl.ncol; ++col)
-      for (int r0 = sl.cs[col]; r0 < sl.cs[col + 1]; r0 += rows_per_tile) ts.push_back(r0);
-    ts.push_back((int)sl.nv);
-    const int T = (int)ts.size() - 1;
-    ts_dev[l].alloc(T + 1, s);
-    ts_dev[l].upload(ts.data(), T + 1);
-    fl_down[l].alloc(T, s);
-    fl_up[l].alloc(T, s);
-    fl_down[l].zero();
-    fl_up[l].zero();
-    DevBuf<int32_t> row2tile;
-    row2tile.alloc(sl.nv, s);
-    row2tile_kernel<<<grid_for(T, 128), 128, 0, s>>>(ts_dev[l].get(), T, row2tile.get());
-    check_launch("row2tile");
-    DevBuf<long long> clo, chi;
-    clo.alloc(sl.nv + 1, s);
-    chi.alloc(sl.nv + 1, s);
-    clo.zero();
-    chi.zero();
-    split_counts_kernel<<<grid_for(sl.nv, 256), 256, 0, s>>>(sl.rp.get(), sl.sp.get(), (int)sl.nv, clo.get(),
-                                                              chi.get());
-    check_launch("split_counts");
-    scan_exclusive_i64((const i64*)clo.get(), (i64*)clo.get(), sl.nv + 1, s);
-    scan_exclusive_i64((const i64*)chi.get(), (i64*)chi.get(), sl.nv + 1, s);
-    const i64 nlo = fetch(clo.get() + sl.nv, s), nhi = fetch(chi.get() + sl.nv, s);
-    DevBuf<u64> klo, khi;
-    klo.alloc(std::max<i64>(nlo, 1), s);
-    khi.alloc(std::max<i64>(nhi, 1), s);
-    dep_pairs_kernel<<<grid_for(sl.nv, 256), 256, 0, s>>>(sl.rp.get(), sl.sp.get(), sl.ci.get(), row2tile.get(),
-                                                          (int)sl.nv, clo.get(), chi.get(), klo.get(), khi.get());
-    check_launch("dep_pairs");
-    auto finish = [&](DevBuf<u64>& k, i64 n, DevBuf<int32_t>& rp, DevBuf<int32_t>& lst) {
-      radix_sort(k.get(), nullptr, n, 32 + bits_for((u64)T), s);
-      const i64 m = unique_sorted(k.get(), n, s);
-      rp.alloc(T + 1, s);
-      rowptr_from_pairs(k.get(), m, T, rp.get(), s);
-      lst.alloc(std::max<i64>(m, 1), s);
-      if (m > 0) {
-        low32_e_kernel<<<grid_for(m, 256), 256, 0, s>>>(k.get(), m, lst.get());
-        check_launch("dep_low32");
+    const int nv = (int)sl.nv, C = sl.ncol;
+    VASMG_CHECK((int)sl.sec.size() == nv, VASMG_ERR_UNSUPPORTED, "missing spatial keys");
+    std::vector<int> RS((size_t)C * (R + 1));
+    std::vector<int> reg(nv);
+    for (int col = 0; col < C; ++col) {
+      const auto b0 = sl.sec.begin() + sl.cs[col], b1 = sl.sec.begin() + sl.cs[col + 1];
+      for (int k = 0; k <= R; ++k) {
+        const uint32_t key = (uint32_t)((i64)k * nv / R);
+        RS[(size_t)col * (R + 1) + k] = (int)(std::lower_bound(b0, b1, key) - sl.sec.begin());
       }
+      for (int k = 0; k < R; ++k)
+        for (int i = RS[(size_t)col * (R + 1) + k]; i < RS[(size_t)col * (R + 1) + k + 1]; ++i) reg[i] = k;
+    }
+    const int W = (R + 63) / 64;
+    auto to_csr = [&](const std::vector<u64>& bits, DevBuf<int32_t>& rp_d, DevBuf<int32_t>& list_d) {
+      std::vector<int> rp(R + 1, 0), list;
+      for (int k = 0; k < R; ++k) {
+        for (int w = 0; w < W; ++w)
+          for (u64 m = bits[(size_t)k * W + w]; m; m &= m - 1) list.push_back(w * 64 + __builtin_ctzll(m));
+        rp[k + 1] = (int)list.size();
+      }
+      if (list.empty()) list.push_back(0);
+      rp_d.alloc(R + 1, s);
+      rp_d.upload(rp.data(), R + 1);
+      list_d.alloc((i64)list.size(), s);
+      list_d.upload(list.data(), (i64)list.size());
     };
-    finish(klo, nlo, dlo_rp[l], dlo[l]);
-    finish(khi, nhi, dhi_rp[l], dhi[l]);
-    lv[l].T = T;
-    lv[l].ts = ts_dev[l].get();
-    lv[l].dlo_rp = dlo_rp[l].get();
-    lv[l].dlo = dlo[l].get();
-    lv[l].dhi_rp = dhi_rp[l].get();
-    lv[l].dhi = dhi[l].get();
-    lv[l].fl_down = fl_down[l].get();
-    lv[l].fl_up = fl_up[l].get();
+    {
+      std::vector<int32_t> rp = sl.rp.download(), ci = sl.ci.download();
+      std::vector<u64> bits((size_t)R * W, 0);
+      for (int i = 0; i < nv; ++i)
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+          const int k2 = reg[ci[e]];
+          if (k2 != reg[i]) bits[(size_t)reg[i] * W + k2 / 64] |= 1ull << (k2 % 64);
+        }
+      to_csr(bits, nb_rp[l], nb[l]);
+    }
+    std::vector<u64> rbits((size_t)R * W, 0);
+    if (l + 1 < L) {
+      const int nvc = (int)c->S[l + 1].nv;
+      std::vector<int32_t> rrp = c->S[l].rrp.download(), rci = c->S[l].rci.download();
+      for (int k = 0; k < R; ++k) {
+        const int I0 = (int)((i64)k * nvc / R), I1 = (int)((i64)(k + 1) * nvc / R);
+        for (int I = I0; I < I1; ++I)
+          for (int t = rrp[I]; t < rrp[I + 1]; ++t) {
+            const int k2 = reg[rci[t]];
+            if (k2 != k) rbits[(size_t)k * W + k2 / 64] |= 1ull << (k2 % 64);
+          }
+      }
+    }
+    to_csr(rbits, rd_rp[l], rd[l]);
+    rs_dev[l].alloc((i64)RS.size(), s);
+    rs_dev[l].upload(RS.data(), (i64)RS.size());
+    pg_d[l].alloc(R, s);
+    pg_u[l].alloc(R, s);
+    pg_d[l].zero();
+    pg_u[l].zero();
+    LV<V>& v = lv[l];
+    v.R = R;
+    v.RS = rs_dev[l].get();
+    v.nb_rp = nb_rp[l].get();
+    v.nb = nb[l].get();
+    v.rd_rp = rd_rp[l].get();
+    v.rd = rd[l].get();
+    v.pg_d = pg_d[l].get();
+    v.pg_u = pg_u[l].get();
   }
 
   void build_sell() {
@@ -1197,13 +1160,13 @@ struct Engine : EngineBase {
     lv.assign(L, LV<V>{});
     G.resize(L);
     cs_dev.resize(L);
-    ts_dev.resize(L);
-    dlo_rp.resize(L);
-    dlo.resize(L);
-    dhi_rp.resize(L);
-    dhi.resize(L);
-    fl_down.resize(L);
-    fl_up.resize(L);
+    rs_dev.resize(L);
+    nb_rp.resize(L);
+    nb.resize(L);
+    rd_rp.resize(L);
+    rd.resize(L);
+    pg_d.resize(L);
+    pg_u.resize(L);
     ctrs.alloc((i64)L * C_N, s);
     {
       std::vector<int> h((size_t)L * C_N, 0);
@@ -1253,16 +1216,14 @@ struct Engine : EngineBase {
       v.rw = rw_ptr(sl);
       v.bc = lv[l + 1].b;
       v.xc = lv[l + 1].x;
-      build_tiles(l);
     }
     lt = L - 1;
     while (lt > 0 && c->S[lt - 1].nv <= TAIL_NV) --lt;
-    // occupancy-sized grids for the self-scheduling launches
+    // one region per co-resident CTA (the launches are cooperative), at
+    // least REGION_MIN_ROWS rows per region
     int dev = 0, sms = 0;
     VASMG_CUDA(cudaGetDevice(&dev));
     VASMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    grid_down.assign(L, 1);
-    grid_up.assign(L, 1);
     for (int l = 0; l + 1 < L; ++l) {
       int bd = 1, bu = 1;
       switch (G[l]) {
@@ -1271,10 +1232,10 @@ struct Engine : EngineBase {
         case 16: occ<16>(&bd, &bu); break;
         default: occ<32>(&bd, &bu); break;
       }
-      const int work_d = 2 * lv[l].T + (int)ceil_div(lv[l].nvc, RC_ROWS);
-      const int work_u = lv[l].T + (int)ceil_div(lv[l].nv, RP_ROWS);
-      grid_down[l] = std::max(1, std::min(bd * sms, work_d));
-      grid_up[l] = std::max(1, std::min(bu * sms, work_u));
+      const i64 cap = (i64)std::min(bd, bu) * sms;
+      VASMG_CHECK(cap >= 1, VASMG_ERR_CUDA, "sweep kernel cannot be resident");
+      const int R = (int)std::max<i64>(1, std::min<i64>(cap, ceil_div(c->S[l].nv, REGION_MIN_ROWS)));
+      build_regions(l, R);
     }
     // tail cluster size: as many CTAs (<= 16) as the work of the tail levels warrants
     {
@@ -1354,25 +1315,39 @@ struct Engine : EngineBase {
   }
 
   // ---------------------------------------------------------------- launches
-  void down(int l, int phases, cudaStream_t s) {
-    const int g = grid_down[l];
-    switch (G[l]) {
-      case 4: vdown_kernel<D, 4, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
-      case 8: vdown_kernel<D, 8, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
-      case 16: vdown_kernel<D, 16, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
-      default: vdown_kernel<D, 32, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
-    }
+  // cooperative launch: every CTA (region) of the grid is resident at once
+  template <typename K>
+  void launch_coop(K kern, int grid, const LV<V>& a, int phases, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(DF_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    Scalars* scp = sc.get();
+    VASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, a, scp, phases));
     ++launch_counter;
   }
-  void up(int l, int phases, cudaStream_t s) {
-    const int g = grid_up[l];
+  void down(int l, int phases, cudaStream_t s) {
+    const int g = lv[l].R;
     switch (G[l]) {
-      case 4: vup_kernel<D, 4, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
-      case 8: vup_kernel<D, 8, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
-      case 16: vup_kernel<D, 16, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
-      default: vup_kernel<D, 32, V, S><<<g, DF_THREADS, 0, s>>>(lv[l], sc.get(), phases); break;
+      case 4: launch_coop(vdown_kernel<D, 4, V, S>, g, lv[l], phases, s); break;
+      case 8: launch_coop(vdown_kernel<D, 8, V, S>, g, lv[l], phases, s); break;
+      case 16: launch_coop(vdown_kernel<D, 16, V, S>, g, lv[l], phases, s); break;
+      default: launch_coop(vdown_kernel<D, 32, V, S>, g, lv[l], phases, s); break;
     }
-    ++launch_counter;
+  }
+  void up(int l, int phases, cudaStream_t s) {
+    const int g = lv[l].R;
+    switch (G[l]) {
+      case 4: launch_coop(vup_kernel<D, 4, V, S>, g, lv[l], phases, s); break;
+      case 8: launch_coop(vup_kernel<D, 8, V, S>, g, lv[l], phases, s); break;
+      case 16: launch_coop(vup_kernel<D, 16, V, S>, g, lv[l], phases, s); break;
+      default: launch_coop(vup_kernel<D, 32, V, S>, g, lv[l], phases, s); break;
+    }
   }
   void tail(int l0, cudaStream_t s) {
     TailArgs<V> ta;

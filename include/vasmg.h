@@ -179,6 +179,39 @@ enum {
 };
 int vasmg_apply(vasmg_handle h, int32_t op, int32_t level, const double* x, double* y);
 
+/* Coarsest-level solve x = A_L^{-1} b that allocates nothing.
+ *
+ * The paper has no counterpart: this is a library-level variant of
+ * vasmg_apply(h, VASMG_OP_COARSE, ...), which stages its vectors through
+ * device buffers it allocates on every call.  Use this entry point where the
+ * caller cannot allocate device memory during the call: a server whose
+ * device memory is budgeted per request, or a latency-bound loop that must
+ * not enter the allocator.
+ *
+ * b, x    device pointers, [n] doubles each, n = dim * (vertices of the
+ *         coarsest level), canonical order (dof = vertex*dim + component), as
+ *         for VASMG_OP_COARSE.  b and x may be the same buffer.
+ * stream  cudaStream_t to run on (NULL: the legacy default stream).
+ *
+ * The work runs asynchronously on `stream`; the call returns once it is
+ * enqueued.  It reads the handle's FP64 Cholesky factor and uses a scratch
+ * array of VASMG_NOALLOC_MAX_DOFS doubles in the library's static device
+ * memory.  Nothing in that scratch needs to start at zero: each call writes
+ * every entry it reads.
+ *
+ * The scratch is shared by every call on the device, so two calls whose
+ * kernels overlap on the GPU (e.g. issued on different streams without
+ * ordering) race and give wrong results; order such calls on one stream or
+ * with events.  The first call on a device looks up the scratch address with
+ * cudaGetSymbolAddress; make one call before capturing a stream that will
+ * contain later calls.
+ *
+ * Returns VASMG_ERR_INVALID_ARG for NULL pointers or when n exceeds
+ * VASMG_NOALLOC_MAX_DOFS (the detail string is not updated on this path),
+ * VASMG_ERR_CUDA if a CUDA call fails. */
+#define VASMG_NOALLOC_MAX_DOFS 4096
+int vasmg_coarse_solve_noalloc(vasmg_handle h, const double* b, double* x, void* stream);
+
 /* Timing helper: launch kernel class `which` (VASMG_KERNEL_*) `reps` times on
  * the handle's stream between two CUDA events; *ms = mean per launch and
  * *bytes = algorithmic bytes that one launch moves. */

@@ -2,6 +2,7 @@
 // entry point catches internal exceptions and returns an error code.
 #include <chrono>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -42,6 +43,39 @@ void destroy_ctx(vasmg_ctx* h) {
     cudaStreamDestroy(s);
   }
   if (ev) cudaEventDestroy(ev);
+}
+
+// Scratch of vasmg_coarse_solve_noalloc: static device memory, so the call
+// never allocates.  Its device address is looked up once per device.
+__device__ __align__(256) double g_noalloc_scratch[VASMG_NOALLOC_MAX_DOFS];
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Forward and backward substitution with the FP64 Cholesky factor (canonical
+// dof order), by one warp; y is the scratch of n doubles.
+__global__ void coarse_noalloc_kernel(const double* __restrict__ chol, const uint8_t* __restrict__ drop, int n,
+                                      const double* b, double* x, double* y) {
+  const int lane = threadIdx.x & 31;
+  for (int t = lane; t < n; t += 32) y[t] = b[t];
+  __syncwarp();
+  for (int j = 0; j < n; ++j) {
+    const double ljj = chol[(long long)j * n + j];
+    const double yj = drop[j] ? 0.0 : y[j] / ljj;
+    __syncwarp();
+    if (lane == 0) y[j] = yj;
+    for (int i = j + 1 + lane; i < n; i += 32) y[i] -= chol[(long long)i * n + j] * yj;
+    __syncwarp();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const double ljj = chol[(long long)j * n + j];
+    const double xj = drop[j] ? 0.0 : y[j] / ljj;
+    __syncwarp();
+    if (lane == 0) y[j] = xj;
+    for (int i = lane; i < j; i += 32) y[i] -= chol[(long long)j * n + i] * xj;
+    __syncwarp();
+  }
+  for (int t = lane; t < n; t += 32) x[t] = y[t];
 }
 
 double now_ms() {
@@ -323,6 +357,27 @@ int vasmg_time_kernel(vasmg_handle h, int32_t which, int32_t level, int32_t reps
   *ms = time_kernel(h->c, which, level, reps, bytes);
   return VASMG_OK;
   VASMG_API_END
+}
+
+int vasmg_coarse_solve_noalloc(vasmg_handle h, const double* b, double* x, void* stream) {
+  if (!h || !b || !x) return VASMG_ERR_INVALID_ARG;
+  const Ctx& c = h->c;
+  const i64 n = c.nc;
+  if (n <= 0 || n > VASMG_NOALLOC_MAX_DOFS) return VASMG_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VASMG_ERR_CUDA;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VASMG_ERR_CUDA;
+      g_noalloc_ptr[dev] = (double*)p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  coarse_noalloc_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(c.chol.get(), c.chol_drop.get(), (int)n, b, x, scratch);
+  return cudaGetLastError() == cudaSuccess ? VASMG_OK : VASMG_ERR_CUDA;
 }
 
 int64_t vasmg_last_launch_count(vasmg_handle h) { return h ? h->c.last_launches : -1; }

@@ -30,7 +30,8 @@ KERNEL_SPMV64, KERNEL_SWEEP, KERNEL_VCYCLE, KERNEL_DOWN, KERNEL_UP = 0, 1, 2, 3,
 # symbols declared in include/vasmg.h
 EXPORTED = ["vasmg_default_options", "vasmg_setup", "vasmg_assemble_load", "vasmg_solve", "vasmg_solve_batch",
             "vasmg_num_levels", "vasmg_level_info", "vasmg_export", "vasmg_apply", "vasmg_time_kernel",
-            "vasmg_last_launch_count", "vasmg_destroy", "vasmg_error_string", "vasmg_last_error_detail"]
+            "vasmg_last_launch_count", "vasmg_destroy", "vasmg_error_string", "vasmg_last_error_detail",
+            "vasmg_coarse_solve_noalloc"]
 
 
 class vasmg_problem(C.Structure):
@@ -84,6 +85,7 @@ def load():
     lib.vasmg_apply.argtypes = [P, C.c_int32, C.c_int32, P, P]
     lib.vasmg_time_kernel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]
+    lib.vasmg_coarse_solve_noalloc.argtypes = [P, P, P, P]
     lib.vasmg_last_launch_count.argtypes = [P]
     lib.vasmg_last_launch_count.restype = C.c_int64
     lib.vasmg_destroy.argtypes = [P]
@@ -202,6 +204,14 @@ def vasmg_time_kernel(h, which: int, level: int = 0, reps: int = 10):
     ms, nbytes = C.c_double(), C.c_double()
     _check(load().vasmg_time_kernel(h, which, level, reps, C.byref(ms), C.byref(nbytes)), "vasmg_time_kernel")
     return ms.value, nbytes.value
+
+
+def vasmg_coarse_solve_noalloc(h, b, x, stream=None):
+    """x = A_L^{-1} b on the coarsest level without allocating (b, x: device
+    tensors of dim * coarsest-vertices doubles, canonical order).  Enqueued on
+    `stream` (an int cudaStream_t or None); the caller synchronises."""
+    s = C.c_void_p(stream) if isinstance(stream, int) else stream
+    _check(load().vasmg_coarse_solve_noalloc(h, _ptr(b), _ptr(x), s), "vasmg_coarse_solve_noalloc")
 
 
 def vasmg_last_launch_count(h) -> int:

@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of one CUDA graph per solve")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no per-kernel roofline timing, e2e, FP64 path or CPU "
                          "baseline); used for profiler launch lists")
@@ -145,6 +146,90 @@ def cpu_oracle_run(n: int, steps: int):
         dt = time.perf_counter() - t0
         vals.append((nfree * it / dt / 1e6, it, dt))
     return vals, nfree
+
+
+def serving_requests(n_req: int, seed: int = 5):
+    """The serving workload: mixed 2D/3D jittered meshes, dofs log-uniform in
+    [5k, 500k], E ~ U[1,100], nu ~ U[0.2,0.45], 1-8 right-hand sides, each the
+    load of a constant body force f ~ U[-1,1]^d."""
+    from paper_2505_09064_gb300 import meshgen
+
+    rs = meshgen.Stream(seed)
+    out = []
+    for i in range(n_req):
+        u = rs.uniform(6)
+        dim = 2 if u[0] < 0.5 else 3
+        dofs = float(np.exp(np.log(5e3) + u[1] * (np.log(5e5) - np.log(5e3))))
+        n = max(4, int(round((dofs / dim) ** (1.0 / dim))))
+        E = 1.0 + 99.0 * u[2]
+        nu = 0.2 + 0.25 * u[3]
+        k = 1 + min(7, int(u[4] * 8))
+        prob = meshgen.make_problem(None, dim=dim, n=n, jitter=0.2 if dim == 2 else 0.15, seed=seed * 1000 + i,
+                                    E=E, nu=nu)
+        forces = rs.uniform(k * dim, -1.0, 1.0).reshape(k, dim)
+        out.append((prob, forces))
+    return out
+
+
+def serving_run(stream, n_req: int = 32):
+    """Continuous-batching server on the serving workload: single-stream
+    capacity, Poisson arrivals at 0.5/0.8/0.95 of it, and the plain FP64
+    one-solve-at-a-time path on the same requests."""
+    from paper_2505_09064_gb300 import meshgen, vasmg
+
+    reqs = serving_requests(n_req)
+    # right-hand sides assembled by the library (outside every timed region)
+    loads = []
+    for prob, forces in reqs:
+        s = vasmg.Solver(prob, precision="fp64", stream=stream)
+        n = prob["coords"].shape[0] * prob["dim"]
+        Fs = []
+        for f in forces:
+            F = np.zeros(n)
+            s.assemble_load(f, F)
+            Fs.append(F)
+        s.close()
+        loads.append(Fs)
+    n_solves = sum(len(F) for F in loads)
+    dofs = [prob["coords"].shape[0] * prob["dim"] for prob, _ in reqs]
+
+    def run(slots, precision, rate=None):
+        srv = vasmg.Server(slots=slots, precision=precision)
+        rs = meshgen.Stream(77)
+        gaps = -np.log(1.0 - rs.uniform(len(reqs))) / rate if rate else np.zeros(len(reqs))
+        t0 = time.perf_counter()
+        tickets, outs = [], []
+        t_next = t0
+        for (prob, _), Fs, g in zip(reqs, loads, gaps):
+            t_next += g
+            while time.perf_counter() < t_next:
+                time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
+            Us = [np.zeros_like(F) for F in Fs]
+            outs.append(Us)
+            tickets.append(srv.submit(prob, Fs, Us))
+        stats = [srv.poll(t, -1) for t in tickets]
+        t1 = time.perf_counter()
+        srv.close()
+        lat = np.array([st["latency_ms"] for st in stats])
+        ok = all(st["status"] == 0 for st in stats)
+        return {"solves_per_s": n_solves / (t1 - t0), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "all_converged": ok,
+                "iterations": int(sum(st["iterations"] for st in stats))}
+
+    run(4, "fp32")  # warm-up: kernels loaded, graphs paths exercised
+    single = run(1, "fp32")
+    cap_rps = len(reqs) / (n_solves / single["solves_per_s"])
+    closed = run(4, "fp32")
+    fp64_single = run(1, "fp64")
+    loads_out = {}
+    for frac in (0.5, 0.8, 0.95):
+        loads_out[str(frac)] = run(4, "fp32", rate=frac * cap_rps)
+    return {"requests": len(reqs), "solves": n_solves, "dofs_min": int(min(dofs)), "dofs_max": int(max(dofs)),
+            "slots": 4, "precision": "fp32 V-cycle, fp64 CG",
+            "single_stream": single, "closed_loop": closed, "fp64_single_stream": fp64_single,
+            "offered_load": loads_out, "capacity_requests_per_s": cap_rps,
+            "recipe": "Poisson arrivals (seed 5/77), mixed 2D/3D jittered P1, 5k-500k dofs log-uniform, "
+                      "E~U[1,100], nu~U[0.2,0.45], 1-8 body-force loads each, tol 1e-6"}
 
 
 def reference_arm(args):
@@ -269,6 +354,9 @@ def ours(args):
         fp64 = {"value": nfree * sum(it64) / (ms64 / 1e3) / 1e6, "iterations": it64[0],
                 "ms_per_solve": ms64 / len(it64)}
         s64.close()
+    serving = None
+    if not args.no_serving:
+        serving = serving_run(stream)
     levels = [vasmg.vasmg_level_info(s.h, l) for l in range(vasmg.vasmg_num_levels(s.h))]
     line = {"metric": "V-ASMG-PCG MDOF*iter/s to 1e-6 rel. residual", "value": value, "unit": "MDOF*iter/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -289,7 +377,7 @@ def ours(args):
                                       for k, v in kernels.items()},
                          "vcycle": {"ms": vc_ms, "bytes": vc_bytes, "gbs": vc_bytes / (vc_ms / 1e3) / 1e9}},
             "e2e": {"value": e2e, "unit": "MDOF*iter/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
-            "gpu_launches": launches, "clocks": clk, "fp64_path": fp64}
+            "gpu_launches": launches, "clocks": clk, "fp64_path": fp64, "serving": serving}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         vals, nf = cpu_oracle_run(SAMPLE_N, 2)
         v = vals[-1]

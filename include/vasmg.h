@@ -40,6 +40,7 @@ extern "C" {
 enum {
   VASMG_OK = 0,
   VASMG_NOT_CONVERGED = 1,
+  VASMG_PENDING = 2,                 /* vasmg_server_poll: the request is not done yet */
   VASMG_ERR_INVALID_ARG = -1,
   VASMG_ERR_DEGENERATE_ELEMENT = -2, /* an element has zero (or non-finite) measure */
   VASMG_ERR_OOM = -3,
@@ -86,6 +87,11 @@ typedef struct {
                                   many dofs (<= 4096) */
   int32_t max_iters;           /* PCG iteration cap, default 1000 */
   int32_t use_graph;           /* 1: one CUDA graph per solve (device-side loop) */
+  int32_t max_ctas;            /* 0: the sweep launches use every CTA slot the
+                                  device can hold at once; > 0: at most this
+                                  many, so that handles whose caps add up to at
+                                  most the device's capacity can solve
+                                  concurrently (vasmg_solve_batch, the server) */
   void* stream;                /* cudaStream_t used for all device work */
 } vasmg_options;
 
@@ -121,9 +127,76 @@ int vasmg_assemble_load(vasmg_handle h, const double* body_force, double* F);
 int vasmg_solve(vasmg_handle h, const double* F, double* U, double tol, vasmg_stats* st);
 
 /* Solve k independent systems (uneven sizes allowed), each to tol, sharing
- * the device; h[i] may repeat.  st may be NULL or an array of k stats. */
+ * the device; h[i] may repeat.  st may be NULL or an array of k stats.
+ *
+ * The solves run concurrently, one host thread and one stream per handle, in
+ * groups whose sweep grids (vasmg_options.max_ctas, as set up) fit the device
+ * together: every CTA of a running sweep launch must be resident at once.
+ * Handles set up with max_ctas = 0 fill the device and run one at a time.  A
+ * handle that appears twice runs in two different groups.  Each result is
+ * the one vasmg_solve gives alone.  Returns the most severe status. */
 int vasmg_solve_batch(int32_t k, const vasmg_handle* h, const double* const* F, double* const* U, double tol,
                       vasmg_stats* st);
+
+/* ------------------------------------------------------------------ serving
+ *
+ * A request server for many independent problems (the paper has no
+ * counterpart; it solves one system at a time).  Requests (one mesh, 1..n
+ * right-hand sides) queue in arrival order.  `slots` worker threads each take
+ * the next request once its estimated device footprint fits the memory
+ * budget left (the head request is admitted alone if it fits nowhere), set up
+ * its hierarchy on the slot's own stream, keep it resident while solving every
+ * right-hand side, write U and release the memory.  Requests on different
+ * slots overlap on the device; every handle's sweep grids are capped to a
+ * share of the device so that all running sweeps stay resident together.
+ * Each result equals what vasmg_setup + vasmg_solve give for that request
+ * alone. */
+typedef struct vasmg_server vasmg_server;
+
+typedef struct {
+  int32_t slots;               /* requests on the device at once; default 4 */
+  int32_t precision;           /* V-cycle precision; default VASMG_FP32_VCYCLE */
+  int32_t max_iters;           /* default 1000 */
+  double tol;                  /* relative residual; default 1e-6 */
+  int64_t memory_budget;       /* device bytes for admitted requests; 0: half
+                                  the free device memory at creation */
+} vasmg_server_opts;
+
+typedef struct {
+  int32_t status;              /* VASMG_OK, VASMG_NOT_CONVERGED or the error of
+                                  the request's setup or solve */
+  int32_t n_rhs;
+  int32_t iterations;          /* summed over the right-hand sides */
+  int32_t max_iterations;
+  double max_rel_res;
+  double queue_ms;             /* submit -> admitted */
+  double setup_ms;
+  double solve_ms;             /* all right-hand sides */
+  double latency_ms;           /* submit -> done */
+  int64_t footprint_bytes;     /* the admission estimate */
+} vasmg_request_stats;
+
+int vasmg_server_default_opts(vasmg_server_opts* out);
+
+/* Start the worker threads on the current device. */
+int vasmg_server_create(const vasmg_server_opts* opts, vasmg_server** out);
+
+/* Queue one request.  The problem arrays and F[0..n_rhs) (host, [n] each) are
+ * copied before the call returns; U[0..n_rhs) are caller-owned host arrays of
+ * [n] doubles that the server writes when the request completes, and that
+ * must stay valid until vasmg_server_poll reports it done.  *ticket names the
+ * request. */
+int vasmg_server_submit(vasmg_server* s, const vasmg_problem* problem, int32_t n_rhs, const double* const* F,
+                        double* const* U, uint64_t* ticket);
+
+/* Wait up to wait_ms milliseconds (< 0: without limit) for a request.
+ * Returns VASMG_PENDING if it is still queued or running, VASMG_OK once it is
+ * done (st, if not NULL, receives its statistics and the ticket is released),
+ * VASMG_ERR_INVALID_ARG for an unknown ticket. */
+int vasmg_server_poll(vasmg_server* s, uint64_t ticket, int32_t wait_ms, vasmg_request_stats* st);
+
+/* Finish every queued request, stop the workers and free the server. */
+int vasmg_server_destroy(vasmg_server* s);
 
 /* Number of levels (fine + coarse). */
 int vasmg_num_levels(vasmg_handle h);

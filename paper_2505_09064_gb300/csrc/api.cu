@@ -3,6 +3,8 @@
 #include <chrono>
 #include <cstring>
 #include <mutex>
+#include <thread>
+#include <vector>
 
 #include "common.cuh"
 
@@ -114,7 +116,8 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   if (opt) o = *opt; else vasmg_default_options(d, &o);
   if (o.n_pre != 1 || o.n_post != 1) return VASMG_ERR_UNSUPPORTED;
   if (o.precision < VASMG_FP64 || o.precision > VASMG_FP32_VCYCLE_BF16_SMOOTH) return VASMG_ERR_INVALID_ARG;
-  if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096 || o.max_iters <= 0) return VASMG_ERR_INVALID_ARG;
+  if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096 || o.max_iters <= 0 || o.max_ctas < 0)
+    return VASMG_ERR_INVALID_ARG;
   vasmg_ctx* h = new vasmg_ctx();
   struct Guard {
     vasmg_ctx*& h;
@@ -132,6 +135,7 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   c.precision = o.precision;
   c.max_iters = o.max_iters;
   c.use_graph = o.use_graph;
+  c.max_ctas = o.max_ctas > 0 ? o.max_ctas : 0;
   c.coarse_max_dofs = o.coarse_max_dofs;
   c.user_stream = (cudaStream_t)o.stream;
   VASMG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
@@ -217,11 +221,55 @@ int vasmg_solve(vasmg_handle h, const double* F, double* U, double tol, vasmg_st
 int vasmg_solve_batch(int32_t k, const vasmg_handle* h, const double* const* F, double* const* U, double tol,
                       vasmg_stats* st) {
   if (k < 0 || (k > 0 && (!h || !F || !U))) return VASMG_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < k; ++i)
+    if (!h[i] || !F[i] || !U[i]) return VASMG_ERR_INVALID_ARG;
+  // groups of handles whose sweep grids are resident together
+  int cap = 0;
+  for (int32_t i = 0; i < k; ++i) {
+    const int ci = h[i]->c.cta_capacity;
+    if (ci > 0) cap = cap ? std::min(cap, ci) : ci;
+  }
+  std::vector<std::vector<int32_t>> groups;
+  std::vector<int> load;
+  for (int32_t i = 0; i < k; ++i) {
+    const int need = std::max(1, h[i]->c.ctas_used);
+    bool placed = false;
+    if (!groups.empty()) {
+      auto& g = groups.back();
+      bool repeat = false;
+      for (int32_t j : g) repeat = repeat || h[j] == h[i];
+      if (!repeat && load.back() + need <= cap) {
+        g.push_back(i);
+        load.back() += need;
+        placed = true;
+      }
+    }
+    if (!placed) {
+      groups.push_back({i});
+      load.push_back(need);
+    }
+  }
+  std::vector<int> rc(k, VASMG_OK);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VASMG_ERR_CUDA;
+  for (const auto& g : groups) {
+    if (g.size() == 1) {
+      const int32_t i = g[0];
+      rc[i] = vasmg_solve(h[i], F[i], U[i], tol, st ? &st[i] : nullptr);
+      continue;
+    }
+    std::vector<std::thread> th;
+    for (int32_t i : g)
+      th.emplace_back([&, i]() {
+        cudaSetDevice(dev);
+        rc[i] = vasmg_solve(h[i], F[i], U[i], tol, st ? &st[i] : nullptr);
+      });
+    for (auto& t : th) t.join();
+  }
   int worst = VASMG_OK;
   for (int32_t i = 0; i < k; ++i) {
-    int rc = vasmg_solve(h[i], F[i], U[i], tol, st ? &st[i] : nullptr);
-    if (rc < 0) return rc;
-    if (rc > worst) worst = rc;
+    if (rc[i] < 0) return rc[i];
+    worst = std::max(worst, rc[i]);
   }
   return worst;
 }

@@ -175,6 +175,9 @@ struct EngineBase;
 
 struct Ctx {
   int dim = 2, K = 31, T = 4, precision = VASMG_FP64, max_iters = 1000, use_graph = 1;
+  int max_ctas = 0;       // cap on the CTAs of one sweep launch (0: device capacity)
+  int ctas_used = 0;      // largest sweep grid this handle launches
+  int cta_capacity = 0;   // CTAs of the sweep kernels the device holds at once
   i64 coarse_max_dofs = 0;
   cudaStream_t stream = 0;       // internal non-blocking stream owned by the handle
   cudaStream_t user_stream = 0;  // caller's stream (options.stream)

@@ -1234,8 +1234,12 @@ struct Engine : EngineBase {
       }
       const i64 cap = (i64)std::min(bd, bu) * sms;
       VASMG_CHECK(cap >= 1, VASMG_ERR_CUDA, "sweep kernel cannot be resident");
-      const int R = (int)std::max<i64>(1, std::min<i64>(cap, ceil_div(c->S[l].nv, REGION_MIN_ROWS)));
+      i64 lim = cap;
+      if (c->max_ctas > 0) lim = std::min<i64>(lim, c->max_ctas);
+      const int R = (int)std::max<i64>(1, std::min<i64>(lim, ceil_div(c->S[l].nv, REGION_MIN_ROWS)));
       build_regions(l, R);
+      c->ctas_used = std::max(c->ctas_used, R);
+      c->cta_capacity = c->cta_capacity ? std::min<int>(c->cta_capacity, (int)cap) : (int)cap;
     }
     // tail cluster size: as many CTAs (<= 16) as the work of the tail levels warrants
     {

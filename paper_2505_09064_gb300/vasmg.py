@@ -31,7 +31,10 @@ KERNEL_SPMV64, KERNEL_SWEEP, KERNEL_VCYCLE, KERNEL_DOWN, KERNEL_UP = 0, 1, 2, 3,
 EXPORTED = ["vasmg_default_options", "vasmg_setup", "vasmg_assemble_load", "vasmg_solve", "vasmg_solve_batch",
             "vasmg_num_levels", "vasmg_level_info", "vasmg_export", "vasmg_apply", "vasmg_time_kernel",
             "vasmg_last_launch_count", "vasmg_destroy", "vasmg_error_string", "vasmg_last_error_detail",
-            "vasmg_coarse_solve_noalloc"]
+            "vasmg_coarse_solve_noalloc", "vasmg_server_default_opts", "vasmg_server_create",
+            "vasmg_server_submit", "vasmg_server_poll", "vasmg_server_destroy"]
+
+OK, NOT_CONVERGED, PENDING = 0, 1, 2
 
 
 class vasmg_problem(C.Structure):
@@ -44,7 +47,19 @@ class vasmg_problem(C.Structure):
 class vasmg_options(C.Structure):
     _fields_ = [("leaf_threshold", C.c_int32), ("n_pre", C.c_int32), ("n_post", C.c_int32),
                 ("precision", C.c_int32), ("coarse_max_dofs", C.c_int64), ("max_iters", C.c_int32),
-                ("use_graph", C.c_int32), ("stream", C.c_void_p)]
+                ("use_graph", C.c_int32), ("max_ctas", C.c_int32), ("stream", C.c_void_p)]
+
+
+class vasmg_server_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("precision", C.c_int32), ("max_iters", C.c_int32), ("tol", C.c_double),
+                ("memory_budget", C.c_int64)]
+
+
+class vasmg_request_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_rhs", C.c_int32), ("iterations", C.c_int32),
+                ("max_iterations", C.c_int32), ("max_rel_res", C.c_double), ("queue_ms", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("latency_ms", C.c_double),
+                ("footprint_bytes", C.c_int64)]
 
 
 class vasmg_stats(C.Structure):
@@ -86,6 +101,11 @@ def load():
     lib.vasmg_time_kernel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]
     lib.vasmg_coarse_solve_noalloc.argtypes = [P, P, P, P]
+    lib.vasmg_server_default_opts.argtypes = [C.POINTER(vasmg_server_opts)]
+    lib.vasmg_server_create.argtypes = [C.POINTER(vasmg_server_opts), C.POINTER(P)]
+    lib.vasmg_server_submit.argtypes = [P, C.POINTER(vasmg_problem), C.c_int32, P, P, C.POINTER(C.c_uint64)]
+    lib.vasmg_server_poll.argtypes = [P, C.c_uint64, C.c_int32, C.POINTER(vasmg_request_stats)]
+    lib.vasmg_server_destroy.argtypes = [P]
     lib.vasmg_last_launch_count.argtypes = [P]
     lib.vasmg_last_launch_count.restype = C.c_int64
     lib.vasmg_destroy.argtypes = [P]
@@ -124,10 +144,8 @@ def vasmg_default_options(dim: int) -> vasmg_options:
     return o
 
 
-def vasmg_setup(prob: dict, options: vasmg_options | None = None):
-    """prob: dict with dim, coords, elems, lam, mu (per element or scalar),
-    dirichlet_dofs, dirichlet_values (optional).  Returns (handle, keepalive)."""
-    lib = load()
+def _problem_struct(prob: dict):
+    """vasmg_problem for a problem dict, and the arrays it points into."""
     dim = int(prob["dim"])
     coords = np.ascontiguousarray(prob["coords"], dtype=np.float64)
     elems = np.ascontiguousarray(prob["elems"], dtype=np.int32)
@@ -139,6 +157,15 @@ def vasmg_setup(prob: dict, options: vasmg_options | None = None):
     dv = None if dv is None else np.ascontiguousarray(dv, dtype=np.float64)
     p = vasmg_problem(dim, coords.shape[0], _ptr(coords), ne, _ptr(elems), _ptr(lam), _ptr(mu), 0.0, 0.0, dd.size,
                       _ptr(dd), _ptr(dv))
+    return p, (coords, elems, lam, mu, dd, dv)
+
+
+def vasmg_setup(prob: dict, options: vasmg_options | None = None):
+    """prob: dict with dim, coords, elems, lam, mu (per element or scalar),
+    dirichlet_dofs, dirichlet_values (optional).  Returns (handle, keepalive)."""
+    lib = load()
+    dim = int(prob["dim"])
+    p, _keep = _problem_struct(prob)
     if options is None:
         options = vasmg_default_options(dim)
     h = C.c_void_p()
@@ -228,7 +255,7 @@ class Solver:
     """Convenience owner of one hierarchy: setup in the constructor, destroy on close."""
 
     def __init__(self, prob: dict, precision: str = "fp64", stream=None, threshold: int = 0,
-                 coarse_max_dofs: int = 0, max_iters: int = 1000, use_graph: bool = True):
+                 coarse_max_dofs: int = 0, max_iters: int = 1000, use_graph: bool = True, max_ctas: int = 0):
         self.dim = int(prob["dim"])
         self.n = int(np.asarray(prob["coords"]).shape[0]) * self.dim
         o = vasmg_default_options(self.dim)
@@ -238,6 +265,7 @@ class Solver:
         o.coarse_max_dofs = coarse_max_dofs
         o.max_iters = max_iters
         o.use_graph = 1 if use_graph else 0
+        o.max_ctas = max_ctas
         o.stream = C.c_void_p(stream) if isinstance(stream, int) else stream
         self.options = o
         self.h = vasmg_setup(prob, o)
@@ -269,3 +297,58 @@ class Solver:
 
     def apply(self, op, level, x, y):
         vasmg_apply(self.h, op, level, x, y)
+
+
+PRECISIONS_SERVER = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+
+class Server:
+    """vasmg_server_*: continuous admission of independent requests.
+
+    submit() copies the problem and the right-hand sides; the U arrays passed
+    in (float64 numpy arrays of n entries) are written by the server and kept
+    referenced here until poll() reports the request done."""
+
+    def __init__(self, slots: int = 4, precision: str = "fp32", tol: float = 1e-6, max_iters: int = 1000,
+                 memory_budget: int = 0):
+        lib = load()
+        o = vasmg_server_opts()
+        _check(lib.vasmg_server_default_opts(C.byref(o)), "vasmg_server_default_opts")
+        o.slots, o.precision, o.tol, o.max_iters, o.memory_budget = (slots, PRECISIONS_SERVER[precision], tol,
+                                                                      max_iters, memory_budget)
+        self.s = C.c_void_p()
+        _check(lib.vasmg_server_create(C.byref(o), C.byref(self.s)), "vasmg_server_create")
+        self._keep = {}
+
+    def submit(self, prob: dict, Fs, Us) -> int:
+        p, keep = _problem_struct(prob)
+        Fs = [np.ascontiguousarray(F, dtype=np.float64) for F in Fs]
+        k = len(Fs)
+        Fp = (C.c_void_p * k)(*[_ptr(F).value for F in Fs])
+        Up = (C.c_void_p * k)(*[_ptr(U).value for U in Us])
+        t = C.c_uint64()
+        _check(load().vasmg_server_submit(self.s, C.byref(p), k, Fp, Up, C.byref(t)), "vasmg_server_submit")
+        self._keep[t.value] = (list(Us), keep)
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = -1):
+        """Stats dict once the request is done, None while it is pending."""
+        st = vasmg_request_stats()
+        rc = load().vasmg_server_poll(self.s, ticket, wait_ms, C.byref(st))
+        if rc == PENDING:
+            return None
+        _check(rc, "vasmg_server_poll")
+        self._keep.pop(ticket, None)
+        return {f: getattr(st, f) for f, _ in vasmg_request_stats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None) is not None and self.s.value:
+            _check(load().vasmg_server_destroy(self.s), "vasmg_server_destroy")
+            self.s = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -54,6 +54,12 @@ def test_host_only_calls(lib):
     assert lib.vasmg_setup(None, None, C.byref(h)) == vasmg.VASMG_ERR_INVALID_ARG
     assert lib.vasmg_num_levels(None) == vasmg.VASMG_ERR_INVALID_ARG
     assert lib.vasmg_destroy(None) == vasmg.VASMG_ERR_INVALID_ARG
+    so = vasmg.vasmg_server_opts()
+    assert lib.vasmg_server_default_opts(C.byref(so)) == 0
+    assert so.slots == 4 and so.tol == 1e-6 and so.precision == 1 and so.memory_budget == 0
+    assert lib.vasmg_server_poll(None, 1, 0, None) == vasmg.VASMG_ERR_INVALID_ARG
+    assert lib.vasmg_server_destroy(None) == vasmg.VASMG_ERR_INVALID_ARG
+    assert lib.vasmg_coarse_solve_noalloc(None, None, None, None) == vasmg.VASMG_ERR_INVALID_ARG
 
 
 def test_struct_layouts_match_header():
@@ -61,8 +67,9 @@ def test_struct_layouts_match_header():
     from paper_2505_09064_gb300 import vasmg
 
     # sizes computed by the C compiler from the header itself
-    prog = ('#include <stdio.h>\n#include "vasmg.h"\nint main(){printf("%zu %zu %zu\\n", sizeof(vasmg_problem), '
-            'sizeof(vasmg_options), sizeof(vasmg_stats));return 0;}\n')
+    prog = ('#include <stdio.h>\n#include "vasmg.h"\nint main(){printf("%zu %zu %zu %zu %zu\\n", '
+            'sizeof(vasmg_problem), sizeof(vasmg_options), sizeof(vasmg_stats), sizeof(vasmg_server_opts), '
+            'sizeof(vasmg_request_stats));return 0;}\n')
     import tempfile
 
     with tempfile.TemporaryDirectory() as td:
@@ -71,4 +78,5 @@ def test_struct_layouts_match_header():
         open(c, "w").write(prog)
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
-    assert sizes == [C.sizeof(vasmg.vasmg_problem), C.sizeof(vasmg.vasmg_options), C.sizeof(vasmg.vasmg_stats)]
+    assert sizes == [C.sizeof(vasmg.vasmg_problem), C.sizeof(vasmg.vasmg_options), C.sizeof(vasmg.vasmg_stats),
+                     C.sizeof(vasmg.vasmg_server_opts), C.sizeof(vasmg.vasmg_request_stats)]

@@ -47,6 +47,7 @@ namespace vasmg {
 constexpr int TAIL_NV = 20000;
 constexpr int TAIL_THREADS = 1024;
 constexpr int TAIL_G = 8;
+constexpr int ONE_CTA_NV = 1200;  // tail levels this small run on one CTA
 constexpr int MAX_LEVELS = 40;
 constexpr int CG_THREADS = 256;
 constexpr int DF_THREADS = 256;
@@ -76,10 +77,18 @@ __device__ __forceinline__ float ldv<float, __nv_bfloat16>(const __nv_bfloat16* 
 }
 
 // vectors written inside a launch by other CTAs are read from L2 (.cg)
-template <typename V>
-__device__ __forceinline__ V ldx(const V* p) { return __ldcg(p); }
-template <typename V>
-__device__ __forceinline__ void stx(V* p, V v) { __stcg(p, v); }
+// LC: the vector is produced and consumed by one CTA only, so plain (L1-cached)
+// accesses are coherent after a CTA barrier.
+template <bool LC = false, typename V>
+__device__ __forceinline__ V ldx(const V* p) {
+  if constexpr (LC) return *p;
+  else return __ldcg(p);
+}
+template <bool LC = false, typename V>
+__device__ __forceinline__ void stx(V* p, V v) {
+  if constexpr (LC) *p = v;
+  else __stcg(p, v);
+}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -144,8 +153,6 @@ struct LV {
   const int* RS;          // [ncol][R+1]: rows of colour c in region k = [RS[c][k], RS[c][k+1])
   const int* nb_rp;       // regions holding a neighbour of a row of region k (CSR, k excluded)
   const int* nb;
-  const int* rd_rp;       // regions holding a fine row that a coarse row of region k restricts
-  const int* rd;
   unsigned long long* pg_d;  // progress of each region in the down launch: epoch << 32 | stage
   unsigned long long* pg_u;  // same for the up launch
   int* ctr;               // C_N counters
@@ -163,7 +170,7 @@ __device__ __forceinline__ float pick(const float (&a)[D], int i) {
 // One row of a sweep / residual by a group of G lanes.
 // MODE 0: x_i = Dinv (b_i - lower part), MODE 1: x_i = Dinv (b_i - all
 // off-diagonal blocks), MODE 2: r_i = -(upper part).
-template <int D, int G, typename V, typename S, int MODE, typename L_t>
+template <int D, int G, typename V, typename S, int MODE, typename L_t, bool LC = false>
 __device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int lane) {
   int k0 = 0, k1 = 0;
   if (valid) {
@@ -178,7 +185,7 @@ __device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int 
     const int j = __ldg(L.ci + k);
     V xj[D];
 #pragma unroll
-    for (int bb = 0; bb < D; ++bb) xj[bb] = ldx(L.x + (long long)j * D + bb);
+    for (int bb = 0; bb < D; ++bb) xj[bb] = ldx<LC>(L.x + (long long)j * D + bb);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -190,14 +197,14 @@ __device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int 
     for (int a = 0; a < D; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o, G);
   if (!valid || lane >= D) return;
   if (MODE == 2) {
-    stx(L.r + (long long)row * D + lane, -pick<D>(acc, lane));
+    stx<LC>(L.r + (long long)row * D + lane, -pick<D>(acc, lane));
   } else {
     V s = V(0);
 #pragma unroll
     for (int bb = 0; bb < D; ++bb)
       s += __ldg((const V*)L.dinv + (long long)(lane * D + bb) * L.nv + row) *
-           (ldx((const V*)L.b + (long long)row * D + bb) - acc[bb]);
-    stx(L.x + (long long)row * D + lane, s);
+           (ldx<LC>((const V*)L.b + (long long)row * D + bb) - acc[bb]);
+    stx<LC>(L.x + (long long)row * D + lane, s);
   }
 }
 
@@ -288,7 +295,7 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
   }
 }
 
-template <int D, typename V, typename L_t>
+template <int D, typename V, typename L_t, bool LC = false>
 __device__ __forceinline__ void restrict_row(const L_t& L, int I) {
   V acc[D];
 #pragma unroll
@@ -297,13 +304,13 @@ __device__ __forceinline__ void restrict_row(const L_t& L, int I) {
     const int i = __ldg(L.rci + t);
     const V w = __ldg((const V*)L.rw + t);
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] += w * ldx((const V*)L.r + (long long)i * D + a);
+    for (int a = 0; a < D; ++a) acc[a] += w * ldx<LC>((const V*)L.r + (long long)i * D + a);
   }
 #pragma unroll
-  for (int a = 0; a < D; ++a) stx((V*)L.bc + (long long)I * D + a, acc[a]);
+  for (int a = 0; a < D; ++a) stx<LC>((V*)L.bc + (long long)I * D + a, acc[a]);
 }
 
-template <int D, typename V, typename L_t>
+template <int D, typename V, typename L_t, bool LC = false>
 __device__ __forceinline__ void prolong_row(const L_t& L, int i) {
   V acc[D];
 #pragma unroll
@@ -312,14 +319,14 @@ __device__ __forceinline__ void prolong_row(const L_t& L, int i) {
     const int J = __ldg(L.pci + t);
     const V w = __ldg((const V*)L.pw + t);
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] += w * ldx((const V*)L.xc + (long long)J * D + a);
+    for (int a = 0; a < D; ++a) acc[a] += w * ldx<LC>((const V*)L.xc + (long long)J * D + a);
   }
   const uint8_t dm = __ldg(L.dead + i);
 #pragma unroll
   for (int a = 0; a < D; ++a)
     if (!((dm >> a) & 1)) {
       V* px = (V*)L.x + (long long)i * D + a;
-      stx(px, ldx((const V*)px) + acc[a]);
+      stx<LC>(px, ldx<LC>((const V*)px) + acc[a]);
     }
 }
 
@@ -406,10 +413,10 @@ __device__ __forceinline__ void rows_pipelined(const LV<V>& L, int r0, int r1, R
 template <int D, typename V>
 constexpr int df_min_blocks() { return (D == 2 && sizeof(V) == 4) ? 3 : 2; }
 
-// phases: 1 forward sweep (zero start), 2 residual, 4 restriction
+// Forward multicolour sweep from zero (pre-smoothing) of one level.
 template <int D, int G, typename V, typename S>
 __global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
-    vdown_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
+    vdown_kernel(const __grid_constant__ LV<V> L, Scalars* sc) {
   __shared__ unsigned s_epoch;
   if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_DEPOCH);
   __syncthreads();
@@ -419,53 +426,23 @@ __global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
   const int nb0 = __ldg(L.nb_rp + k), nnb = __ldg(L.nb_rp + k + 1) - nb0;
   int* abort_flag = &sc->abort;
   unsigned long long* mine = L.pg_d + k;
-  unsigned stage = 0;
-  bool ok = true;
-  if (phases & 1) {
-    for (int c = 0; c < C && ok; ++c) {
-      const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
-      if (r0 < r1) {
-        RowPF<D, V> cur;
-        row_prefetch<D, G, V, S, 0>(L, r0 + g, r0 + g < r1, lane, cur);
-        if (c > 0 && !wait_regions(L.nb + nb0, nnb, L.pg_d, epoch, (unsigned)c, abort_flag)) {
-          ok = false;
-          break;
-        }
-        rows_pipelined<D, G, V, S, 0>(L, r0, r1, cur);
-      }
-      publish_stage(mine, epoch, (unsigned)(c + 1));
+  for (int c = 0; c < C; ++c) {
+    const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+    if (r0 < r1) {
+      RowPF<D, V> cur;
+      row_prefetch<D, G, V, S, 0>(L, r0 + g, r0 + g < r1, lane, cur);
+      if (c > 0 && !wait_regions(L.nb + nb0, nnb, L.pg_d, epoch, (unsigned)c, abort_flag)) break;
+      rows_pipelined<D, G, V, S, 0>(L, r0, r1, cur);
     }
-    stage = (unsigned)C;
-  }
-  if (ok && (phases & 2)) {
-    if (stage > 0 && !wait_regions(L.nb + nb0, nnb, L.pg_d, epoch, stage, abort_flag)) ok = false;
-    if (ok) {
-      for (int c = 0; c < C; ++c) {
-        const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
-        if (r0 < r1) {
-          RowPF<D, V> cur;
-          row_prefetch<D, G, V, S, 2>(L, r0 + g, r0 + g < r1, lane, cur);
-          rows_pipelined<D, G, V, S, 2>(L, r0, r1, cur);
-        }
-      }
-      publish_stage(mine, epoch, ++stage);
-    }
-  }
-  if (ok && (phases & 4)) {
-    const int d0 = __ldg(L.rd_rp + k), nrd = __ldg(L.rd_rp + k + 1) - d0;
-    if (stage > 0 && !wait_regions(L.rd + d0, nrd, L.pg_d, epoch, stage, abort_flag)) ok = false;
-    if (ok) {
-      const int I0 = (int)((long long)k * L.nvc / R), I1 = (int)((long long)(k + 1) * L.nvc / R);
-      for (int I = I0 + (int)threadIdx.x; I < I1; I += blockDim.x) restrict_row<D, V>(L, I);
-    }
+    publish_stage(mine, epoch, (unsigned)(c + 1));
   }
   leave(L.ctr, C_DEXIT, C_DEPOCH);
 }
 
-// phases: 1 prolongation + correction, 2 backward sweep
+// Backward multicolour sweep (post-smoothing) of one level.
 template <int D, int G, typename V, typename S>
 __global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
-    vup_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int phases) {
+    vup_kernel(const __grid_constant__ LV<V> L, Scalars* sc) {
   __shared__ unsigned s_epoch;
   if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_UEPOCH);
   __syncthreads();
@@ -476,26 +453,39 @@ __global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
   int* abort_flag = &sc->abort;
   unsigned long long* mine = L.pg_u + k;
   unsigned stage = 0;
-  if (phases & 1) {
-    for (int c = 0; c < C; ++c) {
-      const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
-      for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) prolong_row<D, V>(L, i);
+  for (int c = C - 1; c >= 0; --c) {
+    const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+    if (r0 < r1) {
+      RowPF<D, V> cur;
+      row_prefetch<D, G, V, S, 1>(L, r0 + g, r0 + g < r1, lane, cur);
+      if (stage > 0 && !wait_regions(L.nb + nb0, nnb, L.pg_u, epoch, stage, abort_flag)) break;
+      rows_pipelined<D, G, V, S, 1>(L, r0, r1, cur);
     }
     publish_stage(mine, epoch, ++stage);
   }
-  if (phases & 2) {
-    for (int c = C - 1; c >= 0; --c) {
-      const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
-      if (r0 < r1) {
-        RowPF<D, V> cur;
-        row_prefetch<D, G, V, S, 1>(L, r0 + g, r0 + g < r1, lane, cur);
-        if (stage > 0 && !wait_regions(L.nb + nb0, nnb, L.pg_u, epoch, stage, abort_flag)) break;
-        rows_pipelined<D, G, V, S, 1>(L, r0, r1, cur);
-      }
-      publish_stage(mine, epoch, ++stage);
-    }
-  }
   leave(L.ctr, C_UEXIT, C_UEPOCH);
+}
+
+// r = -(upper part) x after the zero-start forward sweep: a plain SpMV of
+// the later-colour blocks, G lanes per row, grid-strided over the rows.
+template <int D, int G, typename V, typename S>
+__global__ void __launch_bounds__(256) residual_kernel(const __grid_constant__ LV<V> L) {
+  constexpr int NG = 256 / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  for (int base = blockIdx.x * NG; base < L.nv; base += gridDim.x * NG)
+    row_pass<D, G, V, S, 2>(L, base + g, base + g < L.nv, lane);
+}
+
+// b_{l+1} = R r_l (one thread per coarse row)
+template <int D, typename V>
+__global__ void __launch_bounds__(256) restrict_kernel(const __grid_constant__ LV<V> L) {
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < L.nvc; I += gridDim.x * blockDim.x) restrict_row<D, V>(L, I);
+}
+
+// x_l += P x_{l+1} (one thread per fine row)
+template <int D, typename V>
+__global__ void __launch_bounds__(256) prolong_kernel(const __grid_constant__ LV<V> L) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.nv; i += gridDim.x * blockDim.x) prolong_row<D, V>(L, i);
 }
 
 // ------------------------------------------------------------------ coarsest solve and tail
@@ -509,13 +499,13 @@ struct CoarseArgs {
 };
 
 // Forward / backward substitution with the Cholesky factor, by one warp.
-template <typename V>
+template <typename V, bool LC = false>
 __device__ void coarse_solve_warp(const CoarseArgs& A, const V* b, V* x) {
   const int lane = threadIdx.x & 31;
   const int n = A.n, d = A.d;
   for (int t = lane; t < n; t += 32) {
     const int r = t / d, a = t - r * d;
-    A.y[(long long)__ldg(A.perm + r) * d + a] = (double)ldx(b + t);
+    A.y[(long long)__ldg(A.perm + r) * d + a] = (double)ldx<LC>(b + t);
   }
   __syncwarp();
   for (int j = 0; j < n; ++j) {
@@ -536,7 +526,7 @@ __device__ void coarse_solve_warp(const CoarseArgs& A, const V* b, V* x) {
   }
   for (int t = lane; t < n; t += 32) {
     const int r = t / d, a = t - r * d;
-    stx(x + t, (V)A.y[(long long)__ldg(A.perm + r) * d + a]);
+    stx<LC>(x + t, (V)A.y[(long long)__ldg(A.perm + r) * d + a]);
   }
 }
 
@@ -574,6 +564,7 @@ struct TL {
 template <typename V>
 struct TailArgs {
   int l0, L;                     // levels l0..L handled here, L = coarsest
+  int ls;                        // levels ls..L run on CTA 0 alone
   TL<V> lv[MAX_LEVELS];
   CoarseArgs co;
 };
@@ -593,9 +584,46 @@ __device__ __forceinline__ unsigned cluster_size() {
   return r;
 }
 
+// Levels ls..L of the V-cycle on one CTA: phases separated by CTA barriers,
+// vectors accessed through L1 (no other CTA touches them meanwhile).
+template <int D, typename V, typename S>
+__device__ void tail_one_cta(const TailArgs<V>& A) {
+  constexpr int G = TAIL_G;
+  const int ng = blockDim.x / G, g = (int)threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int ls = A.ls, Lc = A.L;
+  for (int l = ls; l < Lc; ++l) {
+    const TL<V>& L = A.lv[l];
+    for (int c = 0; c < L.ncol; ++c) {
+      const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
+      for (int base = r0; base < r1; base += ng)
+        row_pass<D, G, V, S, 0, TL<V>, true>(L, base + g, base + g < r1, lane);
+      __syncthreads();
+    }
+    for (int base = 0; base < L.nv; base += ng) row_pass<D, G, V, S, 2, TL<V>, true>(L, base + g, base + g < L.nv, lane);
+    __syncthreads();
+    for (int I = tid; I < L.nvc; I += NT) restrict_row<D, V, TL<V>, true>(L, I);
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) coarse_solve_warp<V, true>(A.co, A.lv[Lc].b, A.lv[Lc].x);
+  __syncthreads();
+  for (int l = Lc - 1; l >= ls; --l) {
+    const TL<V>& L = A.lv[l];
+    for (int i = tid; i < L.nv; i += NT) prolong_row<D, V, TL<V>, true>(L, i);
+    __syncthreads();
+    for (int c = L.ncol - 1; c >= 0; --c) {
+      const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
+      for (int base = r0; base < r1; base += ng)
+        row_pass<D, G, V, S, 1, TL<V>, true>(L, base + g, base + g < r1, lane);
+      __syncthreads();
+    }
+  }
+}
+
 // The V-cycle of all small levels in one cluster of CTAs, phases separated by
 // hardware cluster barriers; every group runs the same number of loop trips
-// so the sub-warp shuffles stay converged.
+// so the sub-warp shuffles stay converged.  The smallest levels (ls..L) run
+// on CTA 0 alone between two cluster barriers.
 template <int D, typename V, typename S>
 __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constant__ TailArgs<V> A) {
   constexpr int G = TAIL_G;
@@ -604,8 +632,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constan
   const int gg = rank * ng + (int)threadIdx.x / G, NG = nct * ng;
   const int lane = threadIdx.x & (G - 1);
   const int tid = rank * blockDim.x + threadIdx.x, NT = nct * blockDim.x;
-  const int l0 = A.l0, Lc = A.L;
-  for (int l = l0; l < Lc; ++l) {
+  const int l0 = A.l0, ls = A.ls;
+  for (int l = l0; l < ls; ++l) {
     const TL<V>& L = A.lv[l];
     for (int c = 0; c < L.ncol; ++c) {
       const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
@@ -617,9 +645,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constan
     for (int I = tid; I < L.nvc; I += NT) restrict_row<D, V>(L, I);
     cluster_sync_all();
   }
-  if (rank == 0 && threadIdx.x < 32) coarse_solve_warp<V>(A.co, A.lv[Lc].b, A.lv[Lc].x);
+  if (rank == 0) tail_one_cta<D, V, S>(A);
   cluster_sync_all();
-  for (int l = Lc - 1; l >= l0; --l) {
+  for (int l = ls - 1; l >= l0; --l) {
     const TL<V>& L = A.lv[l];
     for (int i = tid; i < L.nv; i += NT) prolong_row<D, V>(L, i);
     cluster_sync_all();
@@ -991,9 +1019,10 @@ struct Engine : EngineBase {
   int L = 0;       // number of levels
   int lt = 0;      // first tail level
   int nct = 1;     // CTAs in the tail cluster
+  int sms_ = 1;    // SMs of the device
   std::vector<LV<V>> lv;
   std::vector<int> G;
-  std::vector<DevBuf<int32_t>> cs_dev, rs_dev, nb_rp, nb, rd_rp, rd;
+  std::vector<DevBuf<int32_t>> cs_dev, rs_dev, nb_rp, nb;
   std::vector<DevBuf<unsigned long long>> pg_d, pg_u;
   DevBuf<int> ctrs;
   DevBuf<double> coarse_y;
@@ -1083,20 +1112,6 @@ struct Engine : EngineBase {
         }
       to_csr(bits, nb_rp[l], nb[l]);
     }
-    std::vector<u64> rbits((size_t)R * W, 0);
-    if (l + 1 < L) {
-      const int nvc = (int)c->S[l + 1].nv;
-      std::vector<int32_t> rrp = c->S[l].rrp.download(), rci = c->S[l].rci.download();
-      for (int k = 0; k < R; ++k) {
-        const int I0 = (int)((i64)k * nvc / R), I1 = (int)((i64)(k + 1) * nvc / R);
-        for (int I = I0; I < I1; ++I)
-          for (int t = rrp[I]; t < rrp[I + 1]; ++t) {
-            const int k2 = reg[rci[t]];
-            if (k2 != k) rbits[(size_t)k * W + k2 / 64] |= 1ull << (k2 % 64);
-          }
-      }
-    }
-    to_csr(rbits, rd_rp[l], rd[l]);
     rs_dev[l].alloc((i64)RS.size(), s);
     rs_dev[l].upload(RS.data(), (i64)RS.size());
     pg_d[l].alloc(R, s);
@@ -1108,8 +1123,6 @@ struct Engine : EngineBase {
     v.RS = rs_dev[l].get();
     v.nb_rp = nb_rp[l].get();
     v.nb = nb[l].get();
-    v.rd_rp = rd_rp[l].get();
-    v.rd = rd[l].get();
     v.pg_d = pg_d[l].get();
     v.pg_u = pg_u[l].get();
   }
@@ -1163,8 +1176,6 @@ struct Engine : EngineBase {
     rs_dev.resize(L);
     nb_rp.resize(L);
     nb.resize(L);
-    rd_rp.resize(L);
-    rd.resize(L);
     pg_d.resize(L);
     pg_u.resize(L);
     ctrs.alloc((i64)L * C_N, s);
@@ -1224,6 +1235,7 @@ struct Engine : EngineBase {
     int dev = 0, sms = 0;
     VASMG_CUDA(cudaGetDevice(&dev));
     VASMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    sms_ = sms;
     for (int l = 0; l + 1 < L; ++l) {
       int bd = 1, bu = 1;
       switch (G[l]) {
@@ -1321,7 +1333,7 @@ struct Engine : EngineBase {
   // ---------------------------------------------------------------- launches
   // cooperative launch: every CTA (region) of the grid is resident at once
   template <typename K>
-  void launch_coop(K kern, int grid, const LV<V>& a, int phases, cudaStream_t s) {
+  void launch_coop(K kern, int grid, const LV<V>& a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(DF_THREADS);
@@ -1332,25 +1344,53 @@ struct Engine : EngineBase {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     Scalars* scp = sc.get();
-    VASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, a, scp, phases));
+    VASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, a, scp));
     ++launch_counter;
   }
+  int plain_grid(i64 threads) const { return (int)std::max<i64>(1, std::min<i64>(ceil_div(threads, 256), sms_ * 8)); }
+  template <int GG>
+  void residual(int l, cudaStream_t s) {
+    residual_kernel<D, GG, V, S><<<plain_grid((i64)lv[l].nv * GG), 256, 0, s>>>(lv[l]);
+    ++launch_counter;
+  }
+  // phases: 1 forward sweep (zero start), 2 residual, 4 restriction
   void down(int l, int phases, cudaStream_t s) {
     const int g = lv[l].R;
-    switch (G[l]) {
-      case 4: launch_coop(vdown_kernel<D, 4, V, S>, g, lv[l], phases, s); break;
-      case 8: launch_coop(vdown_kernel<D, 8, V, S>, g, lv[l], phases, s); break;
-      case 16: launch_coop(vdown_kernel<D, 16, V, S>, g, lv[l], phases, s); break;
-      default: launch_coop(vdown_kernel<D, 32, V, S>, g, lv[l], phases, s); break;
+    if (phases & 1) {
+      switch (G[l]) {
+        case 4: launch_coop(vdown_kernel<D, 4, V, S>, g, lv[l], s); break;
+        case 8: launch_coop(vdown_kernel<D, 8, V, S>, g, lv[l], s); break;
+        case 16: launch_coop(vdown_kernel<D, 16, V, S>, g, lv[l], s); break;
+        default: launch_coop(vdown_kernel<D, 32, V, S>, g, lv[l], s); break;
+      }
+    }
+    if (phases & 2) {
+      switch (G[l]) {
+        case 4: residual<4>(l, s); break;
+        case 8: residual<8>(l, s); break;
+        case 16: residual<16>(l, s); break;
+        default: residual<32>(l, s); break;
+      }
+    }
+    if (phases & 4) {
+      restrict_kernel<D, V><<<plain_grid(lv[l].nvc), 256, 0, s>>>(lv[l]);
+      ++launch_counter;
     }
   }
+  // phases: 1 prolongation + correction, 2 backward sweep
   void up(int l, int phases, cudaStream_t s) {
-    const int g = lv[l].R;
-    switch (G[l]) {
-      case 4: launch_coop(vup_kernel<D, 4, V, S>, g, lv[l], phases, s); break;
-      case 8: launch_coop(vup_kernel<D, 8, V, S>, g, lv[l], phases, s); break;
-      case 16: launch_coop(vup_kernel<D, 16, V, S>, g, lv[l], phases, s); break;
-      default: launch_coop(vup_kernel<D, 32, V, S>, g, lv[l], phases, s); break;
+    if (phases & 1) {
+      prolong_kernel<D, V><<<plain_grid(lv[l].nv), 256, 0, s>>>(lv[l]);
+      ++launch_counter;
+    }
+    if (phases & 2) {
+      const int g = lv[l].R;
+      switch (G[l]) {
+        case 4: launch_coop(vup_kernel<D, 4, V, S>, g, lv[l], s); break;
+        case 8: launch_coop(vup_kernel<D, 8, V, S>, g, lv[l], s); break;
+        case 16: launch_coop(vup_kernel<D, 16, V, S>, g, lv[l], s); break;
+        default: launch_coop(vup_kernel<D, 32, V, S>, g, lv[l], s); break;
+      }
     }
   }
   void tail(int l0, cudaStream_t s) {
@@ -1358,6 +1398,8 @@ struct Engine : EngineBase {
     std::memset(&ta, 0, sizeof(ta));
     ta.l0 = l0;
     ta.L = L - 1;
+    ta.ls = L - 1;
+    while (ta.ls > l0 && c->S[ta.ls - 1].nv <= ONE_CTA_NV) --ta.ls;
     for (int l = 0; l < L; ++l) {
       const LV<V>& v = lv[l];
       TL<V>& t = ta.lv[l];

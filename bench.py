@@ -62,6 +62,21 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_over_ranks(ms: float, work: float, device=None):
+    """Replicas: the job's time is the slowest rank's, its work the sum of all
+    ranks' work.  Without an initialised process group, the local values."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms, work
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -297,9 +312,7 @@ def ours(args):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
         if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+            torch.distributed.barrier()
         return ms, iters, launches, st
 
     # headline precision
@@ -308,7 +321,7 @@ def ours(args):
     clocks.start()
     ms, iters, launches, st = timed(s, F, U, args.steps)
     clk = clocks.stop()
-    work = nfree * sum(iters) * world
+    ms, work = reduce_over_ranks(ms, float(nfree * sum(iters)), dev)
     value = work / (ms / 1e3) / 1e6
     if args.solve_only:
         if rank == 0:
@@ -345,7 +358,8 @@ def ours(args):
         rc, st2, _ = s.solve(Fh.numpy(), Uh.numpy(), TOL)
         e2e_iters += st2.iterations
     e2e_s = time.perf_counter() - t0
-    e2e = nfree * e2e_iters * world / e2e_s / 1e6
+    e2e_ms, e2e_work = reduce_over_ranks(e2e_s * 1e3, float(nfree * e2e_iters), dev)
+    e2e = e2e_work / (e2e_ms / 1e3) / 1e6
     # the plain FP64 path on the same workload
     fp64 = None
     if args.precision != "fp64":

@@ -47,6 +47,9 @@ def _load():
         lib.or_setup.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, P, P, C.c_int64, P, P, C.c_int, C.c_int64,
                                  P, C.POINTER(C.c_void_p)]
         lib.or_setup.restype = C.c_int
+        lib.or_setup_fine.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, P, P, C.c_int64, P, P, C.c_int,
+                                      C.POINTER(C.c_void_p)]
+        lib.or_setup_fine.restype = C.c_int
         lib.or_destroy.argtypes = [P]
         lib.or_num_levels.argtypes = [P]
         lib.or_level_info.argtypes = [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -75,7 +78,10 @@ def _ptr(a):
 class Oracle:
     """Setup + solve of V-ASMG-PCG on the CPU in FP64 (one hierarchy)."""
 
-    def __init__(self, prob: dict, threshold: int = 0, coarse_max_dofs: int = 0, insertion_order=None):
+    def __init__(self, prob: dict, threshold: int = 0, coarse_max_dofs: int = 0, insertion_order=None,
+                 fine_only: bool = False):
+        """fine_only: assembly, Dirichlet rows and keys only (apply_A(0), the
+        load, keys and sorted-key leaves work; nothing of the hierarchy)."""
         lib = _load()
         self.dim = int(prob["dim"])
         self.coords = np.ascontiguousarray(prob["coords"], dtype=np.float64)
@@ -89,9 +95,13 @@ class Oracle:
         dv = None if dv is None else np.ascontiguousarray(dv, dtype=np.float64)
         order = None if insertion_order is None else np.ascontiguousarray(insertion_order, dtype=np.int64)
         h = C.c_void_p()
-        rc = lib.or_setup(self.dim, self.nv, _ptr(self.coords), self.elems.shape[0], _ptr(self.elems), _ptr(lam),
-                          _ptr(mu), dd.size, _ptr(dd), _ptr(dv), int(threshold), int(coarse_max_dofs), _ptr(order),
-                          C.byref(h))
+        if fine_only:
+            rc = lib.or_setup_fine(self.dim, self.nv, _ptr(self.coords), self.elems.shape[0], _ptr(self.elems),
+                                   _ptr(lam), _ptr(mu), dd.size, _ptr(dd), _ptr(dv), int(threshold), C.byref(h))
+        else:
+            rc = lib.or_setup(self.dim, self.nv, _ptr(self.coords), self.elems.shape[0], _ptr(self.elems), _ptr(lam),
+                              _ptr(mu), dd.size, _ptr(dd), _ptr(dv), int(threshold), int(coarse_max_dofs),
+                              _ptr(order), C.byref(h))
         if rc != 0:
             raise RuntimeError(f"oracle setup failed ({rc})")
         self._h = h

@@ -1012,6 +1012,56 @@ int or_setup(int dim, int64_t nv, const double* X, int64_t ne, const int32_t* E,
   return 0;
 }
 
+// Fine level only: assembly (Sec. 2), Dirichlet rows, bounding square and
+// Morton keys (Sec. 3.1.1 Step 1).  No tree insertion, hierarchy or colouring:
+// enough for A u, the load vector, the keys and the sorted-key leaves of a
+// mesh too large for the full setup.
+int or_setup_fine(int dim, int64_t nv, const double* X, int64_t ne, const int32_t* E, const double* lam,
+                  const double* mu, int64_t ndir, const int64_t* dir_dofs, const double* dir_vals, int threshold,
+                  oracle_t** out) {
+  if ((dim != 2 && dim != 3) || nv <= 0 || ne <= 0 || !X || !E || !lam || !mu || !out) return -1;
+  Oracle* o = new Oracle();
+  o->dim = dim;
+  o->nv = nv;
+  o->ne = ne;
+  o->T = threshold > 0 ? threshold : (dim == 2 ? 4 : 8);
+  o->X.assign(X, X + nv * dim);
+  o->E.assign(E, E + ne * (dim + 1));
+  for (auto v : o->E)
+    if (v < 0 || v >= nv) {
+      delete o;
+      return -1;
+    }
+  o->lam.assign(lam, lam + ne);
+  o->mu.assign(mu, mu + ne);
+  o->is_dir.assign(nv * dim, 0);
+  o->udir.assign(nv * dim, 0.0);
+  for (int64_t k = 0; k < ndir; ++k) {
+    if (dir_dofs[k] < 0 || dir_dofs[k] >= nv * dim) {
+      delete o;
+      return -1;
+    }
+    o->is_dir[dir_dofs[k]] = 1;
+    o->udir[dir_dofs[k]] = dir_vals ? dir_vals[k] : 0.0;
+  }
+  o->K = dim_K(dim);
+  BSR A;
+  int rc = assemble(*o, A);
+  if (rc) {
+    delete o;
+    return rc;
+  }
+  apply_dirichlet(*o, A);
+  bounding_square_and_keys(*o);
+  o->L.clear();
+  o->L.emplace_back();
+  o->L[0].nv = nv;
+  o->L[0].A = std::move(A);
+  o->L[0].dead.assign(o->is_dir.begin(), o->is_dir.end());
+  *out = o;
+  return 0;
+}
+
 void or_destroy(oracle_t* o) { delete o; }
 
 int or_num_levels(const oracle_t* o) { return (int)o->L.size(); }

@@ -109,3 +109,18 @@ def test_linear_displacement_patch_test(oracle_mod, dim, n):
     U, it, rr, st, _ = o.solve(np.zeros(X.shape[0] * dim), tol=1e-13, max_iters=500)
     assert st == 0
     np.testing.assert_allclose(U, u.ravel(), rtol=0, atol=1e-10 * np.abs(u).max())
+
+
+@pytest.mark.parametrize("dim,n,seed", [(2, 17, 5), (3, 6, 6)])
+def test_fine_only_setup_agrees_with_full_setup(oracle_mod, dim, n, seed):
+    """The assembly-only oracle (used at full sizes) gives the operator, load,
+    keys and sorted-key leaves of the full setup, bit for bit."""
+    p = meshgen.make_problem(None, dim=dim, n=n, jitter=0.2, seed=seed)
+    full = oracle_mod.Oracle(p)
+    fine = oracle_mod.Oracle(p, fine_only=True)
+    x = meshgen.Stream(seed).uniform(full.n, -1.0, 1.0)
+    assert np.array_equal(full.apply_A(0, x), fine.apply_A(0, x))
+    assert np.array_equal(full.assemble_load(p["body_force"]), fine.assemble_load(p["body_force"]))
+    assert np.array_equal(full.morton(), fine.morton())
+    assert np.array_equal(full.box(), fine.box())
+    assert np.array_equal(full.leaves(), fine.leaves(True))

@@ -35,6 +35,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "square1024_checker"
 TAIL_NV = 20000         # levels this small run inside the single cluster tail launch
 SAMPLE_N = 192          # CPU sample: same recipe at 192x192 vertices
+# DRAM bytes (read + write) of one launch from an ncu capture of the current
+# kernel (profiles/); absent when the kernel changed after the capture
+TRAFFIC = {}
 TOL = 1e-6
 
 
@@ -331,20 +334,26 @@ def ours(args):
                               "graph": not args.no_graph, "solve_only": True, "clocks": clk}), flush=True)
         s.close()
         return
-    # roofline: every launch class of one iteration timed alone on the library's
-    # stream (CUDA events); the dominant one is reported
+    # roofline: every kernel of one PCG iteration timed alone on the library's
+    # stream (CUDA events, mean over repetitions); the one with the largest
+    # time per iteration is the dominant kernel
     peaks, peak_src = load_peaks()
     nlev = vasmg.vasmg_num_levels(s.h)
-    kernels = {}
-    spmv_ms, spmv_bytes = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_SPMV64, 0, 20)
-    kernels["spmv64_sell"] = (spmv_ms, spmv_bytes)
+    kernels = {"spmv64_sell": vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_SPMV64, 0, 20)}
+    lt = nlev - 1
     for l in range(nlev - 1):
         if levels_vertices(s, l) <= TAIL_NV:
+            lt = l
             break
-        kernels[f"down_l{l}"] = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_DOWN, l, 10)
-        kernels[f"up_l{l}"] = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_UP, l, 10)
+        kernels[f"fwd_sweep_l{l}"] = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_FWD_SWEEP, l, 10)
+        kernels[f"residual_l{l}"] = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_RESIDUAL, l, 10)
+        kernels[f"restrict_l{l}"] = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_RESTRICT, l, 10)
+        kernels[f"prolong_l{l}"] = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_PROLONG, l, 10)
+        kernels[f"bwd_sweep_l{l}"] = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_SWEEP, l, 10)
+    if lt < nlev - 1:
+        kernels[f"tail_l{lt}"] = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_TAIL, lt, 10)
     vc_ms, vc_bytes = vasmg.vasmg_time_kernel(s.h, vasmg.KERNEL_VCYCLE, 0, 10)
-    top = max((k for k in kernels if k != "spmv64_sell"), key=lambda k: kernels[k][0], default="spmv64_sell")
+    top = max(kernels, key=lambda k: kernels[k][0])
     k_ms, k_bytes = kernels[top]
     achieved = k_bytes / (k_ms / 1e3) / 1e9
     # e2e: pinned host F and U, copies inside the timed region
@@ -384,8 +393,9 @@ def ours(args):
                        "level_colours": [lv[2] for lv in levels], "op_complexity": st.op_complexity,
                        "setup_ms": st.setup_ms, "l2": "operators > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "roofline": {"bound": "hbm", "limiter": "latency" if top.startswith("tail") else "latency/HBM",
+                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC.get((args.workload, top)),
                          "kernel": top, "peak_source": peak_src, "launch_ms": k_ms, "algorithmic_bytes": k_bytes,
                          "launches": {k: {"ms": v[0], "bytes": v[1], "gbs": v[1] / (v[0] / 1e3) / 1e9}
                                       for k, v in kernels.items()},

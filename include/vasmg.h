@@ -293,7 +293,13 @@ enum {
   VASMG_KERNEL_SWEEP = 1,        /* one backward multicolour sweep of level `level` */
   VASMG_KERNEL_VCYCLE = 2,       /* one V-cycle from level 0 */
   VASMG_KERNEL_DOWN = 3,         /* pre-smooth + residual + restriction of level `level` */
-  VASMG_KERNEL_UP = 4            /* prolongation + post-smooth of level `level` */
+  VASMG_KERNEL_UP = 4,           /* prolongation + post-smooth of level `level` */
+  VASMG_KERNEL_FWD_SWEEP = 5,    /* one forward multicolour sweep from zero of level `level` */
+  VASMG_KERNEL_RESIDUAL = 6,     /* r = b - A x after the forward sweep, level `level` */
+  VASMG_KERNEL_RESTRICT = 7,     /* b_{l+1} = R r_l */
+  VASMG_KERNEL_PROLONG = 8,      /* x_l += P x_{l+1} */
+  VASMG_KERNEL_TAIL = 9          /* the V-cycle of all levels from `level` down, in the
+                                    single cluster launch that runs the small levels */
 };
 int vasmg_time_kernel(vasmg_handle h, int32_t which, int32_t level, int32_t reps, double* ms, double* bytes);
 

@@ -209,9 +209,9 @@ __device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int 
 }
 
 // Entries a lane keeps in registers between the prefetch and the finish of a row.
-template <int D, typename V>
+template <int D, typename V, int NPF_ = ((D * D * sizeof(V) <= 16) ? 2 : 1)>
 struct RowPF {
-  static constexpr int NPF = (D * D * sizeof(V) <= 16) ? 2 : 1;
+  static constexpr int NPF = NPF_;
   int k0, k1;
   int cj[NPF];
   V a[NPF][D * D];
@@ -222,9 +222,8 @@ struct RowPF {
 // writes during the launch (row range, the first NPF entries of this lane,
 // the diagonal inverse and b); row_finish, called once the tiles this row
 // depends on are done, gathers x and completes the row as row_pass does.
-template <int D, int G, typename V, typename S, int MODE, typename L_t>
-__device__ __forceinline__ void row_prefetch(const L_t& L, int row, bool valid, int lane, RowPF<D, V>& st) {
-  constexpr int NPF = RowPF<D, V>::NPF;
+template <int D, int G, typename V, typename S, int MODE, typename L_t, bool LC = false, int NPF>
+__device__ __forceinline__ void row_prefetch(const L_t& L, int row, bool valid, int lane, RowPF<D, V, NPF>& st) {
   st.k0 = 0;
   st.k1 = 0;
   if (valid) {
@@ -246,14 +245,13 @@ __device__ __forceinline__ void row_prefetch(const L_t& L, int row, bool valid, 
 #pragma unroll
     for (int bb = 0; bb < D; ++bb) {
       st.di[bb] = __ldg((const V*)L.dinv + (long long)(lane * D + bb) * L.nv + row);
-      st.bv[bb] = ldx((const V*)L.b + (long long)row * D + bb);
+      st.bv[bb] = ldx<LC>((const V*)L.b + (long long)row * D + bb);
     }
   }
 }
 
-template <int D, int G, typename V, typename S, int MODE, typename L_t>
-__device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, int lane, const RowPF<D, V>& st) {
-  constexpr int NPF = RowPF<D, V>::NPF;
+template <int D, int G, typename V, typename S, int MODE, typename L_t, bool LC = false, int NPF>
+__device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, int lane, const RowPF<D, V, NPF>& st) {
   V acc[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) acc[a] = V(0);
@@ -262,7 +260,7 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
     if (st.cj[p] >= 0) {
       V xj[D];
 #pragma unroll
-      for (int bb = 0; bb < D; ++bb) xj[bb] = ldx(L.x + (long long)st.cj[p] * D + bb);
+      for (int bb = 0; bb < D; ++bb) xj[bb] = ldx<LC>(L.x + (long long)st.cj[p] * D + bb);
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -274,7 +272,7 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
     const int j = __ldg(L.ci + k);
     V xj[D];
 #pragma unroll
-    for (int bb = 0; bb < D; ++bb) xj[bb] = ldx(L.x + (long long)j * D + bb);
+    for (int bb = 0; bb < D; ++bb) xj[bb] = ldx<LC>(L.x + (long long)j * D + bb);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -286,12 +284,12 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
     for (int a = 0; a < D; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o, G);
   if (!valid || lane >= D) return;
   if (MODE == 2) {
-    stx(L.r + (long long)row * D + lane, -pick<D>(acc, lane));
+    stx<LC>(L.r + (long long)row * D + lane, -pick<D>(acc, lane));
   } else {
     V s = V(0);
 #pragma unroll
     for (int bb = 0; bb < D; ++bb) s += st.di[bb] * (st.bv[bb] - acc[bb]);
-    stx(L.x + (long long)row * D + lane, s);
+    stx<LC>(L.x + (long long)row * D + lane, s);
   }
 }
 
@@ -565,6 +563,7 @@ template <typename V>
 struct TailArgs {
   int l0, L;                     // levels l0..L handled here, L = coarsest
   int ls;                        // levels ls..L run on CTA 0 alone
+  int soff[MAX_LEVELS];          // shared-memory offset (in V) of x_l, b_l, r_l for l >= ls
   TL<V> lv[MAX_LEVELS];
   CoarseArgs co;
 };
@@ -584,39 +583,100 @@ __device__ __forceinline__ unsigned cluster_size() {
   return r;
 }
 
+struct ClusterSync {
+  __device__ __forceinline__ void operator()() const { cluster_sync_all(); }
+};
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// One multicolour sweep of a tail level (MODE 0: forward from zero, MODE 1:
+// backward), colours separated by `sync`.  Group gg of NG handles rows
+// base + gg; the entries, diagonal inverse and b of the next pass (the next
+// colour's first pass at the end of a colour) are loaded before the barrier,
+// since no phase of the sweep writes them; only the x gather follows it.
+template <int D, int G, typename V, typename S, int MODE, bool LC, typename Sync>
+__device__ __forceinline__ void tail_sweep(const TL<V>& L, int gg, int NG, int lane, Sync sync) {
+  const int C = L.ncol;
+  auto colour = [&](int i) { return MODE == 0 ? i : C - 1 - i; };
+  RowPF<D, V, 1> cur;
+  {
+    const int c = colour(0), q0 = __ldg(L.cs + c), q1 = __ldg(L.cs + c + 1);
+    row_prefetch<D, G, V, S, MODE, TL<V>, LC>(L, q0 + gg, q0 + gg < q1, lane, cur);
+  }
+  for (int i = 0; i < C; ++i) {
+    const int c = colour(i), r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
+    for (int base = r0; base < r1; base += NG) {
+      RowPF<D, V, 1> nxt;
+      bool have = false;
+      if (base + NG < r1) {
+        row_prefetch<D, G, V, S, MODE, TL<V>, LC>(L, base + NG + gg, base + NG + gg < r1, lane, nxt);
+        have = true;
+      } else if (i + 1 < C) {
+        const int c2 = colour(i + 1), q0 = __ldg(L.cs + c2), q1 = __ldg(L.cs + c2 + 1);
+        row_prefetch<D, G, V, S, MODE, TL<V>, LC>(L, q0 + gg, q0 + gg < q1, lane, nxt);
+        have = true;
+      }
+      row_finish<D, G, V, S, MODE, TL<V>, LC>(L, base + gg, base + gg < r1, lane, cur);
+      if (have) cur = nxt;
+    }
+    sync();
+  }
+}
+
+// Level l of the one-CTA part with its vectors in shared memory: x, b, r of
+// level l at sm + soff[l] (n_l entries each, in that order).
+template <int D, typename V>
+__device__ __forceinline__ TL<V> shared_level(const TailArgs<V>& A, int l, V* sm) {
+  TL<V> L = A.lv[l];
+  L.x = sm + A.soff[l];
+  L.b = L.x + (long long)A.lv[l].nv * D;
+  L.r = L.b + (long long)A.lv[l].nv * D;
+  if (l < A.L) {
+    L.xc = sm + A.soff[l + 1];
+    L.bc = sm + A.soff[l + 1] + (long long)A.lv[l + 1].nv * D;
+  }
+  return L;
+}
+
 // Levels ls..L of the V-cycle on one CTA: phases separated by CTA barriers,
-// vectors accessed through L1 (no other CTA touches them meanwhile).
+// every vector in shared memory (only b_ls comes in and x_ls goes out), the
+// operators read through L1.
 template <int D, typename V, typename S>
 __device__ void tail_one_cta(const TailArgs<V>& A) {
   constexpr int G = TAIL_G;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  V* sm = reinterpret_cast<V*>(tail_smem);
   const int ng = blockDim.x / G, g = (int)threadIdx.x / G, lane = threadIdx.x & (G - 1);
   const int tid = threadIdx.x, NT = blockDim.x;
   const int ls = A.ls, Lc = A.L;
+  {
+    const TL<V> Ls = shared_level<D, V>(A, ls, sm);
+    for (int t = tid; t < A.lv[ls].nv * D; t += NT) Ls.b[t] = __ldcg(A.lv[ls].b + t);
+  }
+  __syncthreads();
   for (int l = ls; l < Lc; ++l) {
-    const TL<V>& L = A.lv[l];
-    for (int c = 0; c < L.ncol; ++c) {
-      const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
-      for (int base = r0; base < r1; base += ng)
-        row_pass<D, G, V, S, 0, TL<V>, true>(L, base + g, base + g < r1, lane);
-      __syncthreads();
-    }
+    const TL<V> L = shared_level<D, V>(A, l, sm);
+    tail_sweep<D, G, V, S, 0, true>(L, g, ng, lane, CtaSync());
     for (int base = 0; base < L.nv; base += ng) row_pass<D, G, V, S, 2, TL<V>, true>(L, base + g, base + g < L.nv, lane);
     __syncthreads();
     for (int I = tid; I < L.nvc; I += NT) restrict_row<D, V, TL<V>, true>(L, I);
     __syncthreads();
   }
-  if (threadIdx.x < 32) coarse_solve_warp<V, true>(A.co, A.lv[Lc].b, A.lv[Lc].x);
+  {
+    const TL<V> Lcs = shared_level<D, V>(A, Lc, sm);
+    if (threadIdx.x < 32) coarse_solve_warp<V, true>(A.co, Lcs.b, Lcs.x);
+  }
   __syncthreads();
   for (int l = Lc - 1; l >= ls; --l) {
-    const TL<V>& L = A.lv[l];
+    const TL<V> L = shared_level<D, V>(A, l, sm);
     for (int i = tid; i < L.nv; i += NT) prolong_row<D, V, TL<V>, true>(L, i);
     __syncthreads();
-    for (int c = L.ncol - 1; c >= 0; --c) {
-      const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
-      for (int base = r0; base < r1; base += ng)
-        row_pass<D, G, V, S, 1, TL<V>, true>(L, base + g, base + g < r1, lane);
-      __syncthreads();
-    }
+    tail_sweep<D, G, V, S, 1, true>(L, g, ng, lane, CtaSync());
+  }
+  {
+    const TL<V> Ls = shared_level<D, V>(A, ls, sm);
+    for (int t = tid; t < A.lv[ls].nv * D; t += NT) __stcg(A.lv[ls].x + t, Ls.x[t]);
   }
 }
 
@@ -635,11 +695,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constan
   const int l0 = A.l0, ls = A.ls;
   for (int l = l0; l < ls; ++l) {
     const TL<V>& L = A.lv[l];
-    for (int c = 0; c < L.ncol; ++c) {
-      const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
-      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 0>(L, base + gg, base + gg < r1, lane);
-      cluster_sync_all();
-    }
+    tail_sweep<D, G, V, S, 0, false>(L, gg, NG, lane, ClusterSync());
     for (int base = 0; base < L.nv; base += NG) row_pass<D, G, V, S, 2>(L, base + gg, base + gg < L.nv, lane);
     cluster_sync_all();
     for (int I = tid; I < L.nvc; I += NT) restrict_row<D, V>(L, I);
@@ -651,11 +707,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constan
     const TL<V>& L = A.lv[l];
     for (int i = tid; i < L.nv; i += NT) prolong_row<D, V>(L, i);
     cluster_sync_all();
-    for (int c = L.ncol - 1; c >= 0; --c) {
-      const int r0 = __ldg(L.cs + c), r1 = __ldg(L.cs + c + 1);
-      for (int base = r0; base < r1; base += NG) row_pass<D, G, V, S, 1>(L, base + gg, base + gg < r1, lane);
-      cluster_sync_all();
-    }
+    tail_sweep<D, G, V, S, 1, false>(L, gg, NG, lane, ClusterSync());
   }
 }
 
@@ -1020,10 +1072,12 @@ struct Engine : EngineBase {
   int lt = 0;      // first tail level
   int nct = 1;     // CTAs in the tail cluster
   int sms_ = 1;    // SMs of the device
+  size_t tail_smem_set = 0;  // dynamic shared memory the tail kernel is configured for
   std::vector<LV<V>> lv;
   std::vector<int> G;
   std::vector<DevBuf<int32_t>> cs_dev, rs_dev, nb_rp, nb;
   std::vector<DevBuf<unsigned long long>> pg_d, pg_u;
+  std::vector<i64> nnz_lo;        // lower-part (earlier colour) blocks per level
   DevBuf<int> ctrs;
   DevBuf<double> coarse_y;
   // CG
@@ -1103,7 +1157,10 @@ struct Engine : EngineBase {
       list_d.upload(list.data(), (i64)list.size());
     };
     {
-      std::vector<int32_t> rp = sl.rp.download(), ci = sl.ci.download();
+      std::vector<int32_t> rp = sl.rp.download(), ci = sl.ci.download(), spv = sl.sp.download();
+      i64 lo = 0;
+      for (int i = 0; i < nv; ++i) lo += spv[i] - rp[i];
+      nnz_lo[l] = lo;
       std::vector<u64> bits((size_t)R * W, 0);
       for (int i = 0; i < nv; ++i)
         for (int e = rp[i]; e < rp[i + 1]; ++e) {
@@ -1178,6 +1235,7 @@ struct Engine : EngineBase {
     nb.resize(L);
     pg_d.resize(L);
     pg_u.resize(L);
+    nnz_lo.assign(L, 0);
     ctrs.alloc((i64)L * C_N, s);
     {
       std::vector<int> h((size_t)L * C_N, 0);
@@ -1400,6 +1458,17 @@ struct Engine : EngineBase {
     ta.L = L - 1;
     ta.ls = L - 1;
     while (ta.ls > l0 && c->S[ta.ls - 1].nv <= ONE_CTA_NV) --ta.ls;
+    size_t smem = 0;
+    for (int l = ta.ls; l < L; ++l) {
+      ta.soff[l] = (int)(smem / sizeof(V));
+      smem += 3 * sizeof(V) * (size_t)c->S[l].nv * D;
+      smem = (smem + 15) / 16 * 16;
+    }
+    if (smem > tail_smem_set) {
+      VASMG_CHECK(smem <= 200 * 1024, VASMG_ERR_UNSUPPORTED, "tail levels too large for shared memory");
+      VASMG_CUDA(cudaFuncSetAttribute(tail_kernel<D, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      tail_smem_set = smem;
+    }
     for (int l = 0; l < L; ++l) {
       const LV<V>& v = lv[l];
       TL<V>& t = ta.lv[l];
@@ -1430,6 +1499,7 @@ struct Engine : EngineBase {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nct);
     cfg.blockDim = dim3(TAIL_THREADS);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1712,6 +1782,33 @@ struct Engine : EngineBase {
     }
     return b;
   }
+  // single kernels (each array the kernel must touch, each element once)
+  double fwd_bytes(int l) {  // lower blocks, rp/sp, dinv, b read, x written (and gathered)
+    const SolveLevel& sl = c->S[l];
+    const double n = (double)sl.nv * D;
+    return (double)nnz_lo[l] * (D * D * sizeof(S) + 4.0) + 8.0 * sl.nv + (double)sl.nv * D * D * sizeof(V) +
+           3.0 * n * sizeof(V);
+  }
+  double residual_bytes(int l) {  // upper blocks, sp/rp, x read, r written
+    const SolveLevel& sl = c->S[l];
+    const double n = (double)sl.nv * D;
+    return (double)(sl.nnz - nnz_lo[l]) * (D * D * sizeof(S) + 4.0) + 8.0 * sl.nv + 2.0 * n * sizeof(V);
+  }
+  double restrict_bytes(int l) {  // R entries, row pointers, r read, b_{l+1} written
+    const double pn = (double)c->C[l].pnnz;
+    return pn * (4.0 + sizeof(V)) + (c->S[l + 1].nv + 1.0) * 4.0 + (double)c->S[l].nv * D * sizeof(V) +
+           (double)c->S[l + 1].nv * D * sizeof(V);
+  }
+  double prolong_bytes(int l) {  // P entries, row pointers, dead bits, x_{l+1} read, x_l read + written
+    const double pn = (double)c->C[l].pnnz;
+    return pn * (4.0 + sizeof(V)) + (c->S[l].nv + 1.0) * 4.0 + (double)c->S[l].nv +
+           (double)c->S[l + 1].nv * D * sizeof(V) + 2.0 * (double)c->S[l].nv * D * sizeof(V);
+  }
+  double tail_bytes(int l0) {
+    double b = (double)c->nc * c->nc * 8.0;
+    for (int l = l0; l + 1 < L; ++l) b += down_bytes(l) + up_bytes(l);
+    return b;
+  }
   double spmv_bytes() {
     const SolveLevel& sl = c->S[0];
     const double n = (double)sl.nv * D;
@@ -1725,6 +1822,8 @@ struct Engine : EngineBase {
 
   double time(Ctx& ctx, int which, int level, int reps, double* bytes) override {
     cudaStream_t s = c->stream;
+    VASMG_CHECK(which >= VASMG_KERNEL_SPMV64 && which <= VASMG_KERNEL_TAIL, VASMG_ERR_INVALID_ARG, "unknown kernel");
+    VASMG_CHECK(which != VASMG_KERNEL_TAIL || level >= lt, VASMG_ERR_INVALID_ARG, "level is not in the tail launch");
     VASMG_CHECK(which == VASMG_KERNEL_SPMV64 || which == VASMG_KERNEL_VCYCLE || level + 1 < L, VASMG_ERR_INVALID_ARG,
                 "the coarsest level has no sweep");
     clear_abort(s);
@@ -1737,6 +1836,11 @@ struct Engine : EngineBase {
         case VASMG_KERNEL_SWEEP: up(level, 2, s); break;
         case VASMG_KERNEL_DOWN: down(level, 7, s); break;
         case VASMG_KERNEL_UP: up(level, 3, s); break;
+        case VASMG_KERNEL_FWD_SWEEP: down(level, 1, s); break;
+        case VASMG_KERNEL_RESIDUAL: down(level, 2, s); break;
+        case VASMG_KERNEL_RESTRICT: down(level, 4, s); break;
+        case VASMG_KERNEL_PROLONG: up(level, 1, s); break;
+        case VASMG_KERNEL_TAIL: tail(level, s); break;
         default: vcycle(0, s); break;
       }
     };
@@ -1756,6 +1860,11 @@ struct Engine : EngineBase {
       case VASMG_KERNEL_SWEEP: *bytes = sweep_bytes(level); break;
       case VASMG_KERNEL_DOWN: *bytes = down_bytes(level); break;
       case VASMG_KERNEL_UP: *bytes = up_bytes(level); break;
+      case VASMG_KERNEL_FWD_SWEEP: *bytes = fwd_bytes(level); break;
+      case VASMG_KERNEL_RESIDUAL: *bytes = residual_bytes(level); break;
+      case VASMG_KERNEL_RESTRICT: *bytes = restrict_bytes(level); break;
+      case VASMG_KERNEL_PROLONG: *bytes = prolong_bytes(level); break;
+      case VASMG_KERNEL_TAIL: *bytes = tail_bytes(level); break;
       default: *bytes = vcycle_bytes(); break;
     }
     (void)ctx;

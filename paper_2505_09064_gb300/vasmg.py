@@ -26,6 +26,7 @@ PRECISIONS = {"fp64": VASMG_FP64, "fp32": VASMG_FP32_VCYCLE, "bf16": VASMG_FP32_
     0, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16)
 OP_MATVEC, OP_SMOOTH_FWD, OP_SMOOTH_BWD, OP_RESIDUAL, OP_RESTRICT, OP_PROLONG, OP_COARSE, OP_VCYCLE = range(8)
 KERNEL_SPMV64, KERNEL_SWEEP, KERNEL_VCYCLE, KERNEL_DOWN, KERNEL_UP = 0, 1, 2, 3, 4
+KERNEL_FWD_SWEEP, KERNEL_RESIDUAL, KERNEL_RESTRICT, KERNEL_PROLONG, KERNEL_TAIL = 5, 6, 7, 8, 9
 
 # symbols declared in include/vasmg.h
 EXPORTED = ["vasmg_default_options", "vasmg_setup", "vasmg_assemble_load", "vasmg_solve", "vasmg_solve_batch",

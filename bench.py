@@ -37,7 +37,13 @@ TAIL_NV = 20000         # levels this small run inside the single cluster tail l
 SAMPLE_N = 192          # CPU sample: same recipe at 192x192 vertices
 # DRAM bytes (read + write) of one launch from an ncu capture of the current
 # kernel (profiles/); absent when the kernel changed after the capture
-TRAFFIC = {}
+TRAFFIC = {
+    ("square1024_checker", "tail_l4"): 11249664.0,
+    ("square1024_checker", "fwd_sweep_l1"): 215246848.0,
+    ("square1024_checker", "bwd_sweep_l1"): 234793984.0,
+    ("square1024_checker", "residual_l0"): 138429952.0,
+    ("square1024_checker", "spmv64_sell"): 314983424.0,
+}
 TOL = 1e-6
 
 

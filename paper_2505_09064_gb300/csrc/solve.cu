@@ -47,6 +47,9 @@ namespace vasmg {
 constexpr int TAIL_NV = 20000;
 constexpr int TAIL_THREADS = 1024;
 constexpr int TAIL_G = 8;
+// lanes per row in the tail: 3D coarse rows hold ~100 blocks
+template <int D>
+constexpr int tail_g() { return D == 2 ? TAIL_G : 32; }
 constexpr int ONE_CTA_NV = 1200;  // tail levels this small run on one CTA
 constexpr int MAX_LEVELS = 40;
 constexpr int CG_THREADS = 256;
@@ -409,7 +412,7 @@ __device__ __forceinline__ void rows_pipelined(const LV<V>& L, int r0, int r1, R
 
 // Minimum resident CTAs per SM the kernels are compiled for (register cap).
 template <int D, typename V>
-constexpr int df_min_blocks() { return (D == 2 && sizeof(V) == 4) ? 3 : 2; }
+constexpr int df_min_blocks() { return (D == 2 && sizeof(V) == 4) ? 4 : 2; }
 
 // Forward multicolour sweep from zero (pre-smoothing) of one level.
 template <int D, int G, typename V, typename S>
@@ -644,7 +647,7 @@ __device__ __forceinline__ TL<V> shared_level(const TailArgs<V>& A, int l, V* sm
 // operators read through L1.
 template <int D, typename V, typename S>
 __device__ void tail_one_cta(const TailArgs<V>& A) {
-  constexpr int G = TAIL_G;
+  constexpr int G = tail_g<D>();
   extern __shared__ __align__(16) unsigned char tail_smem[];
   V* sm = reinterpret_cast<V*>(tail_smem);
   const int ng = blockDim.x / G, g = (int)threadIdx.x / G, lane = threadIdx.x & (G - 1);
@@ -686,7 +689,7 @@ __device__ void tail_one_cta(const TailArgs<V>& A) {
 // on CTA 0 alone between two cluster barriers.
 template <int D, typename V, typename S>
 __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constant__ TailArgs<V> A) {
-  constexpr int G = TAIL_G;
+  constexpr int G = tail_g<D>();
   const int nct = (int)cluster_size(), rank = (int)cluster_rank();
   const int ng = blockDim.x / G;
   const int gg = rank * ng + (int)threadIdx.x / G, NG = nct * ng;
@@ -1062,7 +1065,8 @@ struct EngineBase {
 static int pick_G(double avg) {
   if (avg <= 6.0) return 4;
   if (avg <= 48.0) return 8;
-  return 16;
+  if (avg <= 64.0) return 16;
+  return 32;
 }
 
 template <int D, typename V, typename S>

@@ -134,6 +134,17 @@ struct LV {
   const int* ci;
   const int* sp;          // first entry of a later colour in each row
   const void* off;        // planes [d*d][nnz] of S
+  // the same blocks split by part, each part contiguous: lower = columns of
+  // earlier colours, upper = later colours (the sweeps and the residual read
+  // only the part they need)
+  const int* rpl;
+  const int* cil;
+  const void* offl;       // planes [d*d][nlo]
+  long long nlo;
+  const int* rph;
+  const int* cih;
+  const void* offh;       // planes [d*d][nhi]
+  long long nhi;
   const V* dinv;          // planes [d*d][nv]
   const uint8_t* dead;    // per vertex, bit a = component a removed
   V* x;
@@ -170,29 +181,89 @@ __device__ __forceinline__ float pick(const float (&a)[D], int i) {
   return D == 2 ? (i == 0 ? a[0] : a[1]) : (i == 0 ? a[0] : (i == 1 ? a[1] : a[D - 1]));
 }
 
+// Entries of one row as a contiguous segment A[a0 .. a0 + len) of the arrays
+// the level and mode select (b0 / B are kept for a second segment and unused).
+struct RowSeg {
+  int a0, la, b0, len;
+};
+
+// A level with split parts (LV): MODE 0 reads the lower part, MODE 2 the
+// upper part, MODE 1 (whole rows) the combined arrays; one segment each.
+template <int MODE, typename S, typename V>
+__device__ __forceinline__ void seg_ptrs(const LV<V>& L, const int*& ciA, const S*& offA, long long& nA,
+                                         const int*& ciB, const S*& offB, long long& nB) {
+  if (MODE == 2) {
+    ciA = L.cih;
+    offA = (const S*)L.offh;
+    nA = L.nhi;
+  } else if (MODE == 0) {
+    ciA = L.cil;
+    offA = (const S*)L.offl;
+    nA = L.nlo;
+  } else {
+    ciA = L.ci;
+    offA = (const S*)L.off;
+    nA = L.nnz;
+  }
+  ciB = ciA;
+  offB = offA;
+  nB = nA;
+}
+template <int MODE, typename V>
+__device__ __forceinline__ RowSeg seg_range(const LV<V>& L, int row) {
+  const int* p = MODE == 2 ? L.rph : (MODE == 0 ? L.rpl : L.rp);
+  RowSeg r;
+  r.a0 = __ldg(p + row);
+  r.la = __ldg(p + row + 1) - r.a0;
+  r.b0 = 0;
+  r.len = r.la;
+  return r;
+}
+
+// Column index and d x d block of entry e of a row.
+template <int D, typename V, typename S>
+__device__ __forceinline__ int seg_entry(const RowSeg& r, int e, const int* ciA, const S* offA, long long nA,
+                                         const int* ciB, const S* offB, long long nB, V (&a)[D * D]) {
+  // every caller passes a single segment (la == len): B is never read
+  const int k = r.a0 + e;
+  const int* cp = ciA;
+  const S* op = offA;
+  const long long n = nA;
+  (void)ciB;
+  (void)offB;
+  (void)nB;
+#pragma unroll
+  for (int q = 0; q < D * D; ++q) a[q] = ldv<V, S>(op + (long long)q * n + k);
+  return __ldg(cp + k);
+}
+
 // One row of a sweep / residual by a group of G lanes.
 // MODE 0: x_i = Dinv (b_i - lower part), MODE 1: x_i = Dinv (b_i - all
 // off-diagonal blocks), MODE 2: r_i = -(upper part).
 template <int D, int G, typename V, typename S, int MODE, typename L_t, bool LC = false>
 __device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int lane) {
-  int k0 = 0, k1 = 0;
-  if (valid) {
-    k0 = MODE == 2 ? __ldg(L.sp + row) : __ldg(L.rp + row);
-    k1 = MODE == 0 ? __ldg(L.sp + row) : __ldg(L.rp + row + 1);
-  }
-  const S* off = (const S*)L.off;
+  RowSeg sg{0, 0, 0, 0};
+  if (valid) sg = seg_range<MODE>(L, row);
+  const int* ciA;
+  const S* offA;
+  long long nA;
+  const int* ciB;
+  const S* offB;
+  long long nB;
+  seg_ptrs<MODE, S>(L, ciA, offA, nA, ciB, offB, nB);
   V acc[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) acc[a] = V(0);
-  for (int k = k0 + lane; k < k1; k += G) {
-    const int j = __ldg(L.ci + k);
+  for (int e = lane; e < sg.len; e += G) {
+    V blk[D * D];
+    const int j = seg_entry<D, V, S>(sg, e, ciA, offA, nA, ciB, offB, nB, blk);
     V xj[D];
 #pragma unroll
     for (int bb = 0; bb < D; ++bb) xj[bb] = ldx<LC>(L.x + (long long)j * D + bb);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int bb = 0; bb < D; ++bb) acc[a] += ldv<V, S>(off + (long long)(a * D + bb) * L.nnz + k) * xj[bb];
+      for (int bb = 0; bb < D; ++bb) acc[a] += blk[a * D + bb] * xj[bb];
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1)
@@ -215,7 +286,7 @@ __device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int 
 template <int D, typename V, int NPF_ = ((D * D * sizeof(V) <= 16) ? 2 : 1)>
 struct RowPF {
   static constexpr int NPF = NPF_;
-  int k0, k1;
+  RowSeg sg;
   int cj[NPF];
   V a[NPF][D * D];
   V di[D], bv[D];
@@ -227,22 +298,20 @@ struct RowPF {
 // depends on are done, gathers x and completes the row as row_pass does.
 template <int D, int G, typename V, typename S, int MODE, typename L_t, bool LC = false, int NPF>
 __device__ __forceinline__ void row_prefetch(const L_t& L, int row, bool valid, int lane, RowPF<D, V, NPF>& st) {
-  st.k0 = 0;
-  st.k1 = 0;
-  if (valid) {
-    st.k0 = MODE == 2 ? __ldg(L.sp + row) : __ldg(L.rp + row);
-    st.k1 = MODE == 0 ? __ldg(L.sp + row) : __ldg(L.rp + row + 1);
-  }
-  const S* off = (const S*)L.off;
+  st.sg = RowSeg{0, 0, 0, 0};
+  if (valid) st.sg = seg_range<MODE>(L, row);
+  const int* ciA;
+  const S* offA;
+  long long nA;
+  const int* ciB;
+  const S* offB;
+  long long nB;
+  seg_ptrs<MODE, S>(L, ciA, offA, nA, ciB, offB, nB);
 #pragma unroll
   for (int p = 0; p < NPF; ++p) {
-    const int k = st.k0 + lane + p * G;
+    const int e = lane + p * G;
     st.cj[p] = -1;
-    if (k < st.k1) {
-      st.cj[p] = __ldg(L.ci + k);
-#pragma unroll
-      for (int q = 0; q < D * D; ++q) st.a[p][q] = ldv<V, S>(off + (long long)q * L.nnz + k);
-    }
+    if (e < st.sg.len) st.cj[p] = seg_entry<D, V, S>(st.sg, e, ciA, offA, nA, ciB, offB, nB, st.a[p]);
   }
   if (MODE != 2 && valid && lane < D) {
 #pragma unroll
@@ -270,16 +339,23 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
         for (int bb = 0; bb < D; ++bb) acc[a] += st.a[p][a * D + bb] * xj[bb];
     }
   }
-  const S* off = (const S*)L.off;
-  for (int k = st.k0 + lane + NPF * G; k < st.k1; k += G) {
-    const int j = __ldg(L.ci + k);
+  const int* ciA;
+  const S* offA;
+  long long nA;
+  const int* ciB;
+  const S* offB;
+  long long nB;
+  seg_ptrs<MODE, S>(L, ciA, offA, nA, ciB, offB, nB);
+  for (int e = lane + NPF * G; e < st.sg.len; e += G) {
+    V blk[D * D];
+    const int j = seg_entry<D, V, S>(st.sg, e, ciA, offA, nA, ciB, offB, nB, blk);
     V xj[D];
 #pragma unroll
     for (int bb = 0; bb < D; ++bb) xj[bb] = ldx<LC>(L.x + (long long)j * D + bb);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int bb = 0; bb < D; ++bb) acc[a] += ldv<V, S>(off + (long long)(a * D + bb) * L.nnz + k) * xj[bb];
+      for (int bb = 0; bb < D; ++bb) acc[a] += blk[a * D + bb] * xj[bb];
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1)
@@ -561,6 +637,26 @@ struct TL {
   V* bc;
   const V* xc;
 };
+
+// A tail level keeps the combined CSR: one segment, [rp, sp) lower, [sp,
+// rp+1) upper.
+template <int MODE, typename S, typename V>
+__device__ __forceinline__ void seg_ptrs(const TL<V>& L, const int*& ciA, const S*& offA, long long& nA,
+                                         const int*& ciB, const S*& offB, long long& nB) {
+  ciA = ciB = L.ci;
+  offA = offB = (const S*)L.off;
+  nA = nB = L.nnz;
+}
+template <int MODE, typename V>
+__device__ __forceinline__ RowSeg seg_range(const TL<V>& L, int row) {
+  RowSeg r;
+  r.a0 = MODE == 2 ? __ldg(L.sp + row) : __ldg(L.rp + row);
+  const int a1 = MODE == 0 ? __ldg(L.sp + row) : __ldg(L.rp + row + 1);
+  r.la = a1 - r.a0;
+  r.b0 = 0;
+  r.len = r.la;
+  return r;
+}
 
 template <typename V>
 struct TailArgs {
@@ -961,6 +1057,30 @@ __global__ void cg_final_kernel(CGArgs a, double* __restrict__ Uout) {
 
 // ------------------------------------------------------------------ setup kernels for the engine
 
+// Copy each row's lower (earlier-colour) and upper (later-colour) blocks into
+// separate contiguous arrays: row i's lower entries start at rpl[i], its upper
+// entries at rph[i].
+template <typename S>
+__global__ void split_parts_kernel(const int* __restrict__ rp, const int* __restrict__ sp,
+                                   const int* __restrict__ ci, const S* __restrict__ off, long long nnz, int dd,
+                                   int nv, const int* __restrict__ rpl, const int* __restrict__ rph,
+                                   int* __restrict__ cil, S* __restrict__ offl, long long nlo,
+                                   int* __restrict__ cih, S* __restrict__ offh, long long nhi) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+    const int k0 = rp[i], ks = sp[i], k1 = rp[i + 1];
+    for (int k = k0; k < ks; ++k) {
+      const long long d = rpl[i] + (k - k0);
+      cil[d] = ci[k];
+      for (int q = 0; q < dd; ++q) offl[(long long)q * nlo + d] = off[(long long)q * nnz + k];
+    }
+    for (int k = ks; k < k1; ++k) {
+      const long long d = rph[i] + (k - ks);
+      cih[d] = ci[k];
+      for (int q = 0; q < dd; ++q) offh[(long long)q * nhi + d] = off[(long long)q * nnz + k];
+    }
+  }
+}
+
 __global__ void low32_e_kernel(const u64* __restrict__ k, i64 n, int* __restrict__ out) {
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     out[i] = (int)(k[i] & 0xffffffffull);
@@ -1082,6 +1202,8 @@ struct Engine : EngineBase {
   std::vector<DevBuf<int32_t>> cs_dev, rs_dev, nb_rp, nb;
   std::vector<DevBuf<unsigned long long>> pg_d, pg_u;
   std::vector<i64> nnz_lo;        // lower-part (earlier colour) blocks per level
+  std::vector<DevBuf<int32_t>> rpl_dev, rph_dev, cil_dev, cih_dev;
+  std::vector<DevBuf<S>> offl_dev, offh_dev;
   DevBuf<int> ctrs;
   DevBuf<double> coarse_y;
   // CG
@@ -1165,6 +1287,38 @@ struct Engine : EngineBase {
       i64 lo = 0;
       for (int i = 0; i < nv; ++i) lo += spv[i] - rp[i];
       nnz_lo[l] = lo;
+      // the blocks split by part (lower / upper), each part contiguous
+      {
+        const i64 hi = sl.nnz - lo;
+        std::vector<int> rpl(nv + 1, 0), rph(nv + 1, 0);
+        for (int i = 0; i < nv; ++i) {
+          rpl[i + 1] = rpl[i] + (spv[i] - rp[i]);
+          rph[i + 1] = rph[i] + (rp[i + 1] - spv[i]);
+        }
+        rpl_dev[l].alloc(nv + 1, s);
+        rpl_dev[l].upload(rpl.data(), nv + 1);
+        rph_dev[l].alloc(nv + 1, s);
+        rph_dev[l].upload(rph.data(), nv + 1);
+        cil_dev[l].alloc(std::max<i64>(lo, 1), s);
+        cih_dev[l].alloc(std::max<i64>(hi, 1), s);
+        offl_dev[l].alloc(std::max<i64>((i64)D * D * lo, 1), s);
+        offh_dev[l].alloc(std::max<i64>((i64)D * D * hi, 1), s);
+        if (nv > 0) {
+          split_parts_kernel<S><<<grid_for(nv, 256), 256, 0, s>>>(
+              sl.rp.get(), sl.sp.get(), sl.ci.get(), (const S*)off_ptr(sl), sl.nnz, D * D, nv, rpl_dev[l].get(),
+              rph_dev[l].get(), cil_dev[l].get(), offl_dev[l].get(), lo, cih_dev[l].get(), offh_dev[l].get(), hi);
+          check_launch("split_parts");
+        }
+        LV<V>& v = lv[l];
+        v.rpl = rpl_dev[l].get();
+        v.cil = cil_dev[l].get();
+        v.offl = offl_dev[l].get();
+        v.nlo = lo;
+        v.rph = rph_dev[l].get();
+        v.cih = cih_dev[l].get();
+        v.offh = offh_dev[l].get();
+        v.nhi = hi;
+      }
       std::vector<u64> bits((size_t)R * W, 0);
       for (int i = 0; i < nv; ++i)
         for (int e = rp[i]; e < rp[i + 1]; ++e) {
@@ -1240,6 +1394,12 @@ struct Engine : EngineBase {
     pg_d.resize(L);
     pg_u.resize(L);
     nnz_lo.assign(L, 0);
+    rpl_dev.resize(L);
+    rph_dev.resize(L);
+    cil_dev.resize(L);
+    cih_dev.resize(L);
+    offl_dev.resize(L);
+    offh_dev.resize(L);
     ctrs.alloc((i64)L * C_N, s);
     {
       std::vector<int> h((size_t)L * C_N, 0);

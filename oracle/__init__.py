@@ -47,6 +47,8 @@ def _load():
         lib.or_setup.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, P, P, C.c_int64, P, P, C.c_int, C.c_int64,
                                  P, C.POINTER(C.c_void_p)]
         lib.or_setup.restype = C.c_int
+        lib.or_set_smoother.argtypes = [P, C.c_int]
+        lib.or_set_smoother.restype = C.c_int
         lib.or_setup_fine.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, P, P, C.c_int64, P, P, C.c_int,
                                       C.POINTER(C.c_void_p)]
         lib.or_setup_fine.restype = C.c_int
@@ -181,6 +183,13 @@ class Oracle:
         y = np.empty_like(x)
         self._lib.or_apply_A(self._h, l, _ptr(x), _ptr(y))
         return y
+
+    def set_smoother(self, smoother: str):
+        """'multicolour' (point-block GS by colours, the GPU path's smoother) or
+        'lexicographic' (the paper's scalar GS in component-major order)."""
+        rc = self._lib.or_set_smoother(self._h, {"multicolour": 0, "lexicographic": 1}[smoother])
+        if rc != 0:
+            raise RuntimeError("or_set_smoother failed")
 
     def gs_sweep(self, l: int, b, x, forward=True):
         b = np.ascontiguousarray(b, dtype=np.float64)

@@ -184,6 +184,7 @@ struct Level {
 
 struct Oracle {
   int dim = 2, K = 31, T = 4;
+  int smoother = 0;               // 0: multicolour point-block GS, 1: scalar lexicographic GS
   i64 nv = 0, ne = 0, coarse_max_dofs = 0;
   std::vector<double> X;
   std::vector<int32_t> E;
@@ -790,6 +791,41 @@ void gs_sweep(const Oracle& o, const Level& lv, const double* b, double* x, bool
   }
 }
 
+// The paper's own smoother (Sec. 2.1, Alg. 1): scalar Gauss-Seidel over the
+// unknowns in component-major order U = (u^1_1 .. u^1_N, u^2_1 .. u^2_N, ..),
+// vertices in the level's own numbering; the backward sweep visits them in
+// reverse order.  Unknown (i, a) is set to
+// (b_ia - sum over (j, b) != (i, a) of A_ij[a][b] x_jb) / A_ii[a][a].
+void gs_lex_sweep(const Oracle& o, const Level& lv, const double* b, double* x, bool forward) {
+  const int d = o.dim;
+  const i64 n = lv.nv * d;
+  for (i64 step = 0; step < n; ++step) {
+    const i64 u = forward ? step : n - 1 - step;
+    const int a = (int)(u / lv.nv);
+    const i64 i = u - (i64)a * lv.nv;
+    double r = b[i * d + a], diag = 0.0;
+    for (i64 k = lv.A.rp[i]; k < lv.A.rp[i + 1]; ++k) {
+      const i64 j = lv.A.ci[k];
+      const double* B = lv.A.blk(k);
+      for (int bb = 0; bb < d; ++bb) {
+        if (j == i && bb == a) {
+          diag = B[a * d + bb];
+          continue;
+        }
+        r -= B[a * d + bb] * x[j * d + bb];
+      }
+    }
+    x[i * d + a] = r / diag;
+  }
+}
+
+void smooth(const Oracle& o, const Level& lv, const double* b, double* x, bool forward) {
+  if (o.smoother == 1)
+    gs_lex_sweep(o, lv, b, x, forward);
+  else
+    gs_sweep(o, lv, b, x, forward);
+}
+
 void restrict_to(const Oracle& o, const Level& fine, const Level& coarse, const double* r, double* bc) {
   const int d = o.dim;
   for (i64 i = 0; i < coarse.nv * d; ++i) bc[i] = 0.0;
@@ -819,7 +855,7 @@ void vcycle(const Oracle& o, size_t l, const double* b, double* x, int n1, int n
     return;
   }
   for (i64 i = 0; i < n; ++i) x[i] = 0.0;
-  for (int s = 0; s < n1; ++s) gs_sweep(o, lv, b, x, true);
+  for (int s = 0; s < n1; ++s) smooth(o, lv, b, x, true);
   std::vector<double> r(n);
   bsr_apply(lv.A, x, r.data());
   for (i64 i = 0; i < n; ++i) r[i] = b[i] - r[i];
@@ -828,7 +864,7 @@ void vcycle(const Oracle& o, size_t l, const double* b, double* x, int n1, int n
   restrict_to(o, lv, cv, r.data(), bc.data());
   vcycle(o, l + 1, bc.data(), ec.data(), n1, n2);
   prolong_add(o, lv, ec.data(), x);
-  for (int s = 0; s < n2; ++s) gs_sweep(o, lv, b, x, false);
+  for (int s = 0; s < n2; ++s) smooth(o, lv, b, x, false);
 }
 
 // ---------------------------------------------------------------- setup driver
@@ -1139,9 +1175,17 @@ int or_apply_A(const oracle_t* o, int l, const double* x, double* y) {
 }
 
 // One multicolour GS sweep on level l, in place on x.
+// Select the smoother of the V-cycle and of or_gs_sweep: 0 multicolour
+// point-block GS (the GPU path's), 1 scalar lexicographic GS (the paper's).
+int or_set_smoother(oracle_t* o, int smoother) {
+  if (!o || smoother < 0 || smoother > 1) return -1;
+  o->smoother = smoother;
+  return 0;
+}
+
 int or_gs_sweep(const oracle_t* o, int l, const double* b, double* x, int forward) {
   if (l < 0 || l >= (int)o->L.size()) return -1;
-  gs_sweep(*o, o->L[l], b, x, forward != 0);
+  smooth(*o, o->L[l], b, x, forward != 0);
   return 0;
 }
 

@@ -190,3 +190,80 @@ def test_iterations_nearly_flat_under_refinement(oracle_mod):
         assert st == 0
         its.append(it)
     assert max(its) <= 16 and max(its) - min(its) <= 5, its
+
+
+@pytest.mark.parametrize("dim,n,seed", [(2, 8, 31), (3, 4, 32)])
+def test_lexicographic_sweep_equals_dense_triangular_solve(oracle_mod, dim, n, seed):
+    """The paper's smoother (Sec. 2.1, Alg. 1): scalar Gauss-Seidel with the
+    unknowns in component-major order.  Writing A in that order as
+    L + D + U (scalar strictly lower, diagonal, strictly upper), one forward
+    sweep from x0 solves (D + L) x1 = b - U x0; a backward sweep swaps L, U."""
+    p = _prob(dim, n, seed)
+    o = oracle_mod.Oracle(p)
+    o.set_smoother("lexicographic")
+    rs = meshgen.Stream(41)
+    for l in range(min(2, o.num_levels)):
+        rp, ci, v = o.operator(l)
+        A = dense_from_bsr(rp, ci, v, dim)  # vertex-major dofs: vertex * dim + a
+        nv = len(rp) - 1
+        # position of vertex-major dof (i, a) in component-major order
+        pos = np.array([a * nv + i for i in range(nv) for a in range(dim)])
+        lower = pos[:, None] > pos[None, :]
+        upper = pos[:, None] < pos[None, :]
+        Dg = np.diag(np.diag(A))
+        b = rs.uniform(nv * dim, -1, 1)
+        x0 = rs.uniform(nv * dim, -1, 1)
+        xf = o.gs_sweep(l, b, x0, forward=True)
+        ref_f = np.linalg.solve(Dg + A * lower, b - (A * upper) @ x0)
+        np.testing.assert_allclose(xf, ref_f, rtol=1e-10, atol=1e-10 * np.abs(ref_f).max())
+        xb = o.gs_sweep(l, b, x0, forward=False)
+        ref_b = np.linalg.solve(Dg + A * upper, b - (A * lower) @ x0)
+        np.testing.assert_allclose(xb, ref_b, rtol=1e-10, atol=1e-10 * np.abs(ref_b).max())
+
+
+@pytest.mark.parametrize("dim,n,seed", [(2, 9, 5), (3, 5, 6)])
+def test_lexicographic_vcycle_symmetric_and_solves(oracle_mod, dim, n, seed):
+    """With forward pre- and backward post-smoothing the lexicographic V-cycle
+    is symmetric positive definite too, and PCG with it reaches the dense
+    direct solution."""
+    p = _prob(dim, n, seed)
+    o = oracle_mod.Oracle(p)
+    o.set_smoother("lexicographic")
+    nv = p["coords"].shape[0]
+    rs = meshgen.Stream(43)
+    dirm = np.zeros(nv * dim, bool)
+    dirm[p["dirichlet_dofs"]] = True
+    for _ in range(3):
+        x = rs.uniform(nv * dim, -1, 1)
+        y = rs.uniform(nv * dim, -1, 1)
+        x[dirm] = 0
+        y[dirm] = 0
+        Mx, My = o.vcycle(x), o.vcycle(y)
+        assert abs(x @ My - y @ Mx) <= 1e-12 * np.sqrt((x @ Mx) * (y @ My))
+        assert x @ Mx > 0
+    F = o.assemble_load(p["body_force"])
+    U, it, rr, st, _ = o.solve(F, tol=1e-10)
+    assert st == 0 and it > 0
+    rp, ci, v = o.operator(0)
+    A = dense_from_bsr(rp, ci, v, dim)
+    Fr = F.copy()
+    Fr[dirm] = 0.0
+    Uref = np.linalg.solve(A, Fr)
+    assert np.abs(U - Uref).max() <= 1e-8 * np.abs(Uref).max()
+
+
+@pytest.mark.parametrize("dim,n,seed", [(2, 33, 61), (3, 9, 62)])
+def test_multicolour_costs_few_iterations_over_lexicographic(oracle_mod, dim, n, seed):
+    """The GPU path's smoother (multicolour point-block GS) against the
+    paper's (scalar lexicographic GS, Sec. 2.1): on the same hierarchy both
+    V-cycle preconditioners converge, within a few iterations of each other."""
+    p = _prob(dim, n, seed)
+    o = oracle_mod.Oracle(p)
+    F = o.assemble_load(p["body_force"])
+    its = {}
+    for sm in ("multicolour", "lexicographic"):
+        o.set_smoother(sm)
+        _, it, rr, st, _ = o.solve(F, tol=1e-6)
+        assert st == 0 and rr < 1e-6
+        its[sm] = it
+    assert abs(its["multicolour"] - its["lexicographic"]) <= 4, its

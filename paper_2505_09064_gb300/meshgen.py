@@ -228,3 +228,140 @@ def random_problem(seed: int, dim: int | None = None, n_range=(3, 12)):
     nu = 0.2 + 0.25 * u[3]
     jit = (0.2 if dim == 2 else 0.15) * u[4]
     return make_problem(None, dim=dim, n=n, jitter=jit, seed=seed, E=E, nu=nu)
+
+
+# ---------------------------------------------------------------- the paper's 2D examples (Sec. 5)
+#
+# Mapped structured P1 meshes of the four 2D geometries of Sec. 5 (Examples
+# 4.1-4.4), with their boundary conditions.  The paper's own unstructured meshes
+# are not available, so the vertex counts follow its tables instead.  Line
+# forces are given to the solver as a load vector of nodal forces: a uniform
+# traction q on a boundary edge of length l puts q l / 2 on each of its ends.
+
+PAPER_EXAMPLES = {
+    # name: (paper example, vertices in the paper's table, V-ASMG iterations in the paper's table)
+    "hole_round": ("4.1 round-hole plate", 99054, 9),
+    "ring": ("4.2 quarter ring", 150129, 11),
+    "hole_square": ("4.3 square-hole plate", 200185, 10),
+    "dam": ("4.4 thin-walled water retaining structure", 249278, 12),
+}
+
+
+def _grid_triangles(P: np.ndarray):
+    """Vertices P[a, b] (a-major) of a mapped grid; each cell split in two
+    triangles along alternating diagonals, all counter-clockwise."""
+    n1, n2 = P.shape[:2]
+    coords = np.ascontiguousarray(P.reshape(-1, 2))
+    a, b = np.meshgrid(np.arange(n1 - 1), np.arange(n2 - 1), indexing="ij")
+    v00 = (a * n2 + b).ravel()
+    v01 = v00 + 1
+    v10 = v00 + n2
+    v11 = v10 + 1
+    alt = ((a + b) % 2 == 0).ravel()
+    t1 = np.where(alt[:, None], np.stack([v00, v10, v11], 1), np.stack([v00, v10, v01], 1))
+    t2 = np.where(alt[:, None], np.stack([v00, v11, v01], 1), np.stack([v10, v11, v01], 1))
+    elems = np.empty((2 * v00.size, 3), dtype=np.int32)
+    elems[0::2] = t1
+    elems[1::2] = t2
+    neg = _signed_measure(coords, elems) < 0
+    elems[neg] = elems[neg][:, [0, 2, 1]]
+    if not np.all(_signed_measure(coords, elems) > 0):
+        raise RuntimeError("degenerate mapped mesh")
+    return coords, elems
+
+
+def _edge_load(coords: np.ndarray, chain: np.ndarray, q) -> np.ndarray:
+    """Nodal forces of a uniform traction q along the boundary polyline
+    through the vertices `chain` (in order)."""
+    F = np.zeros(coords.shape[0] * 2)
+    x = coords[chain]
+    seg = np.linalg.norm(x[1:] - x[:-1], axis=1)
+    for c in range(2):
+        np.add.at(F, chain[:-1] * 2 + c, 0.5 * q[c] * seg)
+        np.add.at(F, chain[1:] * 2 + c, 0.5 * q[c] * seg)
+    return F
+
+
+def _graded(n: int, ratio: float) -> np.ndarray:
+    """n points on [0, 1], spacing growing geometrically by `ratio` overall."""
+    if ratio == 1.0:
+        return np.linspace(0.0, 1.0, n)
+    g = ratio ** (1.0 / (n - 2))
+    t = (g ** np.arange(n) - 1.0) / (g ** (n - 1) - 1.0)
+    t[-1] = 1.0
+    return t
+
+
+def paper_example(name: str, scale: float = 1.0) -> dict:
+    """One of the paper's 2D examples (E = 2.1e5, nu = 0.3) with about
+    `scale` times the paper's vertex count.  Returns the problem dict of
+    make_problem with the load vector in key "F" (body_force is zero)."""
+    E, nu = 2.1e5, 0.3
+    nvert = max(200, int(PAPER_EXAMPLES[name][1] * scale))
+    if name in ("hole_round", "hole_square"):
+        # O-grid of the top-right quarter of the 10 x 10 plate around the hole
+        nt = int(np.sqrt(nvert)) | 1          # odd: the corner (10, 10) is a grid line
+        nr = max(3, nvert // nt)
+        th = np.linspace(0.0, np.pi / 2, nt)
+        rho = _graded(nr, 10.0)
+        c, s = np.cos(th), np.sin(th)
+        c[-1], s[0] = 0.0, 0.0
+        lower = th <= np.pi / 4
+        half = nt // 2
+        outer = np.where(lower[:, None], np.stack([np.full(nt, 10.0), 10.0 * np.tan(th)], 1),
+                         np.stack([10.0 * c / np.where(s > 0, s, 1.0), np.full(nt, 10.0)], 1))
+        outer[half] = (10.0, 10.0)
+        outer[-1] = (0.0, 10.0)
+        outer[0] = (10.0, 0.0)
+        if name == "hole_round":
+            inner = np.stack([c, s], 1)
+        else:
+            inner = np.where(lower[:, None], np.stack([np.ones(nt), np.tan(th)], 1),
+                             np.stack([c / np.where(s > 0, s, 1.0), np.ones(nt)], 1))
+            inner[half] = (1.0, 1.0)
+            inner[-1] = (0.0, 1.0)
+            inner[0] = (1.0, 0.0)
+        P = inner[:, None, :] + rho[None, :, None] * (outer - inner)[:, None, :]
+        coords, elems = _grid_triangles(P)
+        vid = np.arange(nt * nr).reshape(nt, nr)
+        left = vid[-1, :]              # x = 0: u1 = 0
+        bottom = vid[0, :]             # y = 0: u2 = 0
+        dd = np.concatenate([left * 2, bottom * 2 + 1]).astype(np.int64)
+        F = _edge_load(coords, vid[: half + 1, -1], (10.0, 0.0))   # x = 10: q1 = 10
+        lam_c, mu_c = lame(E, nu)
+    elif name == "ring":
+        # quarter ring 1 <= r <= 10, left boundary clamped, bottom loaded
+        nt = int(np.sqrt(nvert))
+        nr = max(3, nvert // nt)
+        th = np.linspace(0.0, np.pi / 2, nt)
+        r = 10.0 ** np.linspace(0.0, 1.0, nr)
+        c, s = np.cos(th), np.sin(th)
+        c[-1], s[0] = 0.0, 0.0
+        P = np.stack([c[:, None] * r[None, :], s[:, None] * r[None, :]], -1)
+        coords, elems = _grid_triangles(P)
+        vid = np.arange(nt * nr).reshape(nt, nr)
+        left = vid[-1, :]              # x = 0: u1 = u2 = 0
+        dd = np.concatenate([left * 2, left * 2 + 1]).astype(np.int64)
+        F = _edge_load(coords, vid[0, :], (0.0, -10.0))            # y = 0: q2 = -10
+        lam_c, mu_c = lame(E, nu)
+    elif name == "dam":
+        # trapezoid: height 20, bottom width 10, top width 3, left side vertical
+        ny = int(np.sqrt(2 * nvert))
+        nx = max(3, nvert // ny)
+        y = np.linspace(0.0, 20.0, ny)
+        t = np.linspace(0.0, 1.0, nx)
+        xr = 10.0 - 7.0 * y / 20.0
+        P = np.stack([t[None, :] * xr[:, None], np.broadcast_to(y[:, None], (ny, nx))], -1)
+        coords, elems = _grid_triangles(P)
+        vid = np.arange(ny * nx).reshape(ny, nx)
+        bottom = vid[0, :]             # y = 0: u1 = u2 = 0
+        dd = np.concatenate([bottom * 2, bottom * 2 + 1]).astype(np.int64)
+        F = _edge_load(coords, vid[:, 0], (10.0, 0.0))             # x = 0: q1 = 10
+        lam3, mu_c = lame(E, nu)
+        lam_c = 2.0 * lam3 * mu_c / (lam3 + 2.0 * mu_c)           # plane stress
+    else:
+        raise KeyError(name)
+    ne = elems.shape[0]
+    F[dd] = 0.0
+    return dict(dim=2, coords=coords, elems=elems, lam=np.full(ne, float(lam_c)), mu=np.full(ne, float(mu_c)),
+                dirichlet_dofs=np.unique(dd), dirichlet_values=None, body_force=np.zeros(2), F=F)

@@ -115,6 +115,22 @@ int vasmg_default_options(int dim, vasmg_options* out);
  * VASMG_ERR_INVALID_ARG for out-of-range ids or sizes. */
 int vasmg_setup(const vasmg_problem* problem, const vasmg_options* options, vasmg_handle* out);
 
+/* New material data or new Dirichlet values for the same mesh and the same
+ * set of Dirichlet dofs, reusing the hierarchy.  The region tree, coarse
+ * grids and transfers (Sec. 3.1, 3.2), the sparsity patterns, colourings,
+ * renumbering and the solve engine's layout depend only on the mesh and on
+ * which dofs are constrained; only values are recomputed: the assembly
+ * (Sec. 2), the Dirichlet lift, the Galerkin products (eq. (Ac)), the
+ * diagonal inverses and the coarsest Cholesky factor.
+ *   lambda, mu        [n_elements] host arrays, or NULL for lambda_const /
+ *                     mu_const on every element
+ *   dirichlet_values  [n_dirichlet] host array in the order of the dofs given
+ *                     to vasmg_setup, or NULL to keep the current values
+ * Later solves give what a fresh vasmg_setup with the new data would give.
+ * VASMG_ERR_INVALID_ARG for a NULL handle or non-finite parameters. */
+int vasmg_update_data(vasmg_handle h, const double* lambda, const double* mu, double lambda_const, double mu_const,
+                      const double* dirichlet_values);
+
 /* F = consistent load of a constant body force f (Sec. 2, F_1, F_2):
  * F_i += f |K| / (dim+1) over the elements K containing vertex i.
  * body_force: host [dim].  F: host or device [n]. */

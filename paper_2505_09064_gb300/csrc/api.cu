@@ -148,6 +148,7 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   // inputs
   std::vector<uint8_t> isdir((size_t)c.n, 0);
   std::vector<double> udir((size_t)c.n, 0.0);
+  c.dir_dofs.assign(pb->dirichlet_dofs, pb->dirichlet_dofs + pb->n_dirichlet);
   for (int64_t k = 0; k < pb->n_dirichlet; ++k) {
     const int64_t g = pb->dirichlet_dofs[k];
     VASMG_CHECK(g >= 0 && g < c.n, VASMG_ERR_INVALID_ARG, "Dirichlet dof out of range");
@@ -182,6 +183,41 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   c.setup_ms = now_ms() - t0;
   *out = h;
   guard.armed = false;
+  return VASMG_OK;
+  VASMG_API_END
+}
+
+int vasmg_update_data(vasmg_handle h, const double* lambda, const double* mu, double lambda_const, double mu_const,
+                      const double* dirichlet_values) {
+  if (!h) return VASMG_ERR_INVALID_ARG;
+  VASMG_API_BEGIN
+  const double t0 = now_ms();
+  Ctx& c = h->c;
+  join_user(c);
+  cudaStream_t s = c.stream;
+  std::vector<double> lam((size_t)c.ne), mu_v((size_t)c.ne);
+  for (int64_t e = 0; e < c.ne; ++e) {
+    lam[e] = lambda ? lambda[e] : lambda_const;
+    mu_v[e] = mu ? mu[e] : mu_const;
+    VASMG_CHECK(std::isfinite(lam[e]) && std::isfinite(mu_v[e]), VASMG_ERR_INVALID_ARG, "non-finite Lame parameter");
+  }
+  c.lam.upload(lam.data(), c.ne);
+  c.mu.upload(mu_v.data(), c.ne);
+  if (dirichlet_values) {
+    std::vector<double> udir((size_t)c.n, 0.0);
+    c.has_dir_values = false;
+    for (size_t k = 0; k < c.dir_dofs.size(); ++k) {
+      udir[(size_t)c.dir_dofs[k]] = dirichlet_values[k];
+      if (dirichlet_values[k] != 0.0) c.has_dir_values = true;
+    }
+    c.udir.upload(udir.data(), c.n);
+  }
+  assemble_values(c);
+  for (int l = 0; l + 1 < (int)c.C.size(); ++l) galerkin_values(c, l);
+  solve_level_values(c);
+  refresh_solver_values(c);
+  VASMG_CUDA(cudaStreamSynchronize(s));
+  c.update_ms = now_ms() - t0;
   return VASMG_OK;
   VASMG_API_END
 }

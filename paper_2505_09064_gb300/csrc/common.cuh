@@ -140,6 +140,10 @@ struct CanonLevel {
   i64 pnnz = 0;
   DevBuf<int32_t> prp, pci;
   DevBuf<double> pw;
+  // R = P^T as (coarse row, fine entry) pairs, kept for recomputing the
+  // Galerkin values of the next level when the material changes
+  DevBuf<u64> r_keys;
+  DevBuf<int32_t> r_ent, r_rp;
   // colouring
   DevBuf<int32_t> colour;
   int ncol = 0;
@@ -154,6 +158,7 @@ struct SolveLevel {
   int ncol = 0;
   std::vector<int32_t> cs;      // host copy of colour starts [ncol+1]
   std::vector<uint32_t> sec;    // host: spatial key of each solve row (ascending within a colour)
+  DevBuf<int32_t> ent;          // canonical block entry of each solve-order off-diagonal entry
   DevBuf<int32_t> perm, iperm;  // solve index -> canonical, canonical -> solve
   DevBuf<int32_t> rp, ci, sp;   // sp[i]: first entry of row i whose column is of a later colour
   DevBuf<double> off64;         // [d*d][nnz]
@@ -190,6 +195,8 @@ struct Ctx {
   DevBuf<uint8_t> isdir;
   DevBuf<double> udir, lift;
   bool has_dir_values = false;
+  std::vector<int64_t> dir_dofs;  // host: the Dirichlet dofs in the caller's order
+  double update_ms = 0;           // wall-clock of the last vasmg_update_data
   // vertex -> element incidence
   DevBuf<int32_t> inc_rp, inc_e;
   // region tree
@@ -224,6 +231,12 @@ void assemble_load_dev(Ctx& c, const double* f, double* F_dev);
 void setup_tree(Ctx& c);                           // setup_tree.cu
 void setup_galerkin(Ctx& c, int l);                // setup_galerkin.cu
 void setup_colour_and_solve_levels(Ctx& c);        // setup_colour.cu
+// numeric stages only (the structure from setup stays): for new Lame
+// parameters or Dirichlet values
+void assemble_values(Ctx& c);                      // setup_assemble.cu
+void galerkin_values(Ctx& c, int l);               // setup_galerkin.cu
+void solve_level_values(Ctx& c);                   // setup_colour.cu
+void refresh_solver_values(Ctx& c);                // solve.cu
 void setup_solver_state(Ctx& c);                   // solve.cu
 // solve
 int solve_dev(Ctx& c, const double* F_dev, double* U_dev, double tol, vasmg_stats* st);

@@ -242,9 +242,21 @@ void setup_assemble(Ctx& c) {
     low32_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys.get(), nnz, L0.ci.get());
     check_launch("low32");
   }
-  L0.v.alloc(L0.nnzb * d * d, s);
+  assemble_values(c);
+}
+
+// Block values of A (Sec. 2) on the pattern built above, the Dirichlet lift
+// A u_D and the identity rows/columns of the Dirichlet dofs.
+void assemble_values(Ctx& c) {
+  cudaStream_t s = c.stream;
+  const int d = c.dim;
+  CanonLevel& L0 = c.C[0];
+  DevBuf<int> bad;
+  bad.alloc(1, s);
+  bad.zero();
+  if (L0.v.n != L0.nnzb * d * d) L0.v.alloc(L0.nnzb * d * d, s);
   L0.v.zero();
-  c.vol.alloc(c.ne, s);
+  if (c.vol.n != c.ne) c.vol.alloc(c.ne, s);
   if (d == 2)
     assemble_values_kernel<2><<<grid_for(c.nv, 128), 128, 0, s>>>(c.X.get(), c.E.get(), c.lam.get(), c.mu.get(),
                                                                      c.inc_rp.get(), c.inc_e.get(), L0.rp.get(),
@@ -259,14 +271,14 @@ void setup_assemble(Ctx& c) {
   VASMG_CHECK(fetch(bad.get(), s) == 0, VASMG_ERR_DEGENERATE_ELEMENT, "element with zero or non-finite measure");
 
   // Dirichlet: keep A u_D for the reduced right-hand side, then identity rows/columns
-  c.lift.alloc(c.n, s);
+  if (c.lift.n != c.n) c.lift.alloc(c.n, s);
   canon_spmv_kernel<<<grid_for(c.nv, 128), 128, 0, s>>>(L0.rp.get(), L0.ci.get(), L0.v.get(), c.udir.get(),
                                                          c.lift.get(), c.nv, d);
   check_launch("lift");
   dirichlet_rows_kernel<<<grid_for(c.nv, 128), 128, 0, s>>>(L0.rp.get(), L0.ci.get(), L0.v.get(), c.isdir.get(),
                                                              c.nv, d);
   check_launch("dirichlet_rows");
-  L0.dead.alloc(c.n, s);
+  if (L0.dead.n != c.n) L0.dead.alloc(c.n, s);
   VASMG_CUDA(cudaMemcpyAsync(L0.dead.get(), c.isdir.get(), c.n, cudaMemcpyDeviceToDevice, s));
 }
 

@@ -424,44 +424,11 @@ void setup_colour_and_solve_levels(Ctx& c) {
       check_launch("low32");
       split_kernel<<<grid_for(cl.nv, 256), 256, 0, s>>>(sl.rp.get(), sl.ci.get(), cl.nv, sl.sp.get());
       check_launch("split");
-      // value planes in the precisions the solve needs
-      const bool need64 = l == 0 || c.precision == VASMG_FP64;
-      if (need64) {
-        sl.off64.alloc((i64)dd * sl.nnz, s);
-        planes_kernel<double><<<grid_for(sl.nnz, 256), 256, 0, s>>>(cl.v.get(), ent.get(), sl.nnz, dd, sl.off64.get());
-        check_launch("planes64");
-      }
-      if (c.precision == VASMG_FP32_VCYCLE) {
-        sl.off32.alloc((i64)dd * sl.nnz, s);
-        planes_kernel<float><<<grid_for(sl.nnz, 256), 256, 0, s>>>(cl.v.get(), ent.get(), sl.nnz, dd, sl.off32.get());
-        check_launch("planes32");
-      }
-      if (c.precision == VASMG_FP32_VCYCLE_BF16_SMOOTH) {
-        sl.off16.alloc((i64)dd * sl.nnz, s);
-        planes_kernel<__nv_bfloat16><<<grid_for(sl.nnz, 256), 256, 0, s>>>(cl.v.get(), ent.get(), sl.nnz, dd,
-                                                                             sl.off16.get());
-        check_launch("planes16");
-      }
+      sl.ent = std::move(ent);
     }
     sl.deadbits.alloc(cl.nv, s);
     deadbits_kernel<<<grid_for(cl.nv, 256), 256, 0, s>>>(cl.dead.get(), sl.perm.get(), cl.nv, d, sl.deadbits.get());
     check_launch("deadbits");
-    // diagonal blocks and inverses
-    {
-      if (l == 0) sl.diag64.alloc((i64)dd * cl.nv, s);
-      sl.dinv64.alloc((i64)dd * cl.nv, s);
-      sl.dinv32.alloc((i64)dd * cl.nv, s);
-      cl.dinv.alloc((i64)dd * cl.nv, s);
-      if (d == 2)
-        diag_kernel<2><<<grid_for(cl.nv, 256), 256, 0, s>>>(cl.rp.get(), cl.ci.get(), cl.v.get(), sl.perm.get(), cl.nv,
-                                                             l == 0 ? sl.diag64.get() : nullptr, sl.dinv64.get(),
-                                                             sl.dinv32.get(), cl.dinv.get());
-      else
-        diag_kernel<3><<<grid_for(cl.nv, 256), 256, 0, s>>>(cl.rp.get(), cl.ci.get(), cl.v.get(), sl.perm.get(), cl.nv,
-                                                             l == 0 ? sl.diag64.get() : nullptr, sl.dinv64.get(),
-                                                             sl.dinv32.get(), cl.dinv.get());
-      check_launch("diag");
-    }
   }
   // transfers in solve order
   for (int l = 0; l + 1 < L; ++l) {
@@ -502,20 +469,68 @@ void setup_colour_and_solve_levels(Ctx& c) {
                                                           sf.rw64.get(), sf.rw32.get());
     check_launch("r_fill");
   }
-  // coarsest dense Cholesky (canonical order of the last level)
-  {
-    CanonLevel& cl = c.C[L - 1];
-    c.nc = cl.nv * d;
-    VASMG_CHECK(c.nc <= 4096, VASMG_ERR_UNSUPPORTED, "coarsest level larger than 4096 dofs");
-    c.chol.alloc(c.nc * c.nc, s);
-    c.chol.zero();
-    c.chol_drop.alloc(c.nc, s);
-    dense_kernel<<<grid_for(cl.nv, 64), 64, 0, s>>>(cl.rp.get(), cl.ci.get(), cl.v.get(), cl.nv, d, c.chol.get());
-    check_launch("dense");
-    cholesky_kernel<<<1, 1024, 0, s>>>(c.chol.get(), c.nc, c.chol_drop.get());
-    check_launch("cholesky");
-  }
+  solve_level_values(c);
   VASMG_CUDA(cudaStreamSynchronize(s));
+}
+
+// Values of every level in solve order -- off-diagonal planes in the
+// precisions the solve needs, diagonal blocks and their inverses -- and the
+// coarsest Cholesky factor.  Buffers are allocated on the first call and
+// refilled in place afterwards (the solve engine keeps their addresses).
+void solve_level_values(Ctx& c) {
+  cudaStream_t s = c.stream;
+  const int d = c.dim, dd = d * d;
+  const int L = (int)c.C.size();
+  auto ensure = [&](auto& buf, i64 n) {
+    if (buf.n != n) buf.alloc(n, s);
+  };
+  for (int l = 0; l < L; ++l) {
+    CanonLevel& cl = c.C[l];
+    SolveLevel& sl = c.S[l];
+    const bool need64 = l == 0 || c.precision == VASMG_FP64;
+    if (need64) {
+      ensure(sl.off64, (i64)dd * sl.nnz);
+      planes_kernel<double><<<grid_for(sl.nnz, 256), 256, 0, s>>>(cl.v.get(), sl.ent.get(), sl.nnz, dd,
+                                                                   sl.off64.get());
+      check_launch("planes64");
+    }
+    if (c.precision == VASMG_FP32_VCYCLE) {
+      ensure(sl.off32, (i64)dd * sl.nnz);
+      planes_kernel<float><<<grid_for(sl.nnz, 256), 256, 0, s>>>(cl.v.get(), sl.ent.get(), sl.nnz, dd,
+                                                                  sl.off32.get());
+      check_launch("planes32");
+    }
+    if (c.precision == VASMG_FP32_VCYCLE_BF16_SMOOTH) {
+      ensure(sl.off16, (i64)dd * sl.nnz);
+      planes_kernel<__nv_bfloat16><<<grid_for(sl.nnz, 256), 256, 0, s>>>(cl.v.get(), sl.ent.get(), sl.nnz, dd,
+                                                                           sl.off16.get());
+      check_launch("planes16");
+    }
+    if (l == 0) ensure(sl.diag64, (i64)dd * cl.nv);
+    ensure(sl.dinv64, (i64)dd * cl.nv);
+    ensure(sl.dinv32, (i64)dd * cl.nv);
+    ensure(cl.dinv, (i64)dd * cl.nv);
+    if (d == 2)
+      diag_kernel<2><<<grid_for(cl.nv, 256), 256, 0, s>>>(cl.rp.get(), cl.ci.get(), cl.v.get(), sl.perm.get(), cl.nv,
+                                                           l == 0 ? sl.diag64.get() : nullptr, sl.dinv64.get(),
+                                                           sl.dinv32.get(), cl.dinv.get());
+    else
+      diag_kernel<3><<<grid_for(cl.nv, 256), 256, 0, s>>>(cl.rp.get(), cl.ci.get(), cl.v.get(), sl.perm.get(), cl.nv,
+                                                           l == 0 ? sl.diag64.get() : nullptr, sl.dinv64.get(),
+                                                           sl.dinv32.get(), cl.dinv.get());
+    check_launch("diag");
+  }
+  // coarsest dense Cholesky (canonical order of the last level)
+  CanonLevel& cl = c.C[L - 1];
+  c.nc = cl.nv * d;
+  VASMG_CHECK(c.nc <= 4096, VASMG_ERR_UNSUPPORTED, "coarsest level larger than 4096 dofs");
+  ensure(c.chol, c.nc * c.nc);
+  c.chol.zero();
+  ensure(c.chol_drop, c.nc);
+  dense_kernel<<<grid_for(cl.nv, 64), 64, 0, s>>>(cl.rp.get(), cl.ci.get(), cl.v.get(), cl.nv, d, c.chol.get());
+  check_launch("dense");
+  cholesky_kernel<<<1, 1024, 0, s>>>(c.chol.get(), c.nc, c.chol_drop.get());
+  check_launch("cholesky");
 }
 
 }  // namespace vasmg

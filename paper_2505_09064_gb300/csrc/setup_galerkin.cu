@@ -150,30 +150,38 @@ void setup_galerkin(Ctx& c, int l) {
   low32_i_kernel<<<grid_for(g.nnzb, 256), 256, 0, s>>>(keys.get(), g.nnzb, g.ci.get());
   check_launch("low32");
   keys.release();
-  // ---- R = P^T as (coarse row, fine index) sorted pairs
-  DevBuf<u64> rkeys;
-  DevBuf<int32_t> rent, rrp;
-  rkeys.alloc(f.pnnz, s);
-  rent.alloc(f.pnnz, s);
-  transpose_keys_kernel<<<grid_for(f.nv, 256), 256, 0, s>>>(f.prp.get(), f.pci.get(), f.nv, rkeys.get(), rent.get());
+  // ---- R = P^T as (coarse row, fine index) sorted pairs, kept on the fine level
+  f.r_keys.alloc(f.pnnz, s);
+  f.r_ent.alloc(f.pnnz, s);
+  transpose_keys_kernel<<<grid_for(f.nv, 256), 256, 0, s>>>(f.prp.get(), f.pci.get(), f.nv, f.r_keys.get(),
+                                                             f.r_ent.get());
   check_launch("transpose_keys");
-  radix_sort(rkeys.get(), rent.get(), f.pnnz, 32 + bits_for((u64)g.nv), s);
-  rrp.alloc(g.nv + 1, s);
-  rowptr_from_pairs(rkeys.get(), f.pnnz, g.nv, rrp.get(), s);
-  // ---- numeric
-  g.v.alloc(g.nnzb * d * d, s);
+  radix_sort(f.r_keys.get(), f.r_ent.get(), f.pnnz, 32 + bits_for((u64)g.nv), s);
+  f.r_rp.alloc(g.nv + 1, s);
+  rowptr_from_pairs(f.r_keys.get(), f.pnnz, g.nv, f.r_rp.get(), s);
+  galerkin_values(c, l);
+}
+
+// ---- numeric: A_{l+1} = P^T A_l P on the pattern built above (eq. (Ac)),
+// with dead-dof masks; also run again when A_l's values change.
+void galerkin_values(Ctx& c, int l) {
+  cudaStream_t s = c.stream;
+  const int d = c.dim;
+  CanonLevel& f = c.C[l];
+  CanonLevel& g = c.C[l + 1];
+  if (g.v.n != g.nnzb * d * d) g.v.alloc(g.nnzb * d * d, s);
   g.v.zero();
-  g.dead.alloc(g.nv * d, s);
+  if (g.dead.n != g.nv * d) g.dead.alloc(g.nv * d, s);
   if (d == 2)
-    gal_values_kernel<2><<<grid_for(g.nv, 128), 128, 0, s>>>(g.nv, rrp.get(), rent.get(), rkeys.get(), f.prp.get(),
-                                                              f.pci.get(), f.pw.get(), f.rp.get(), f.ci.get(),
-                                                              f.v.get(), f.dead.get(), g.rp.get(), g.ci.get(),
-                                                              g.v.get(), g.dead.get());
+    gal_values_kernel<2><<<grid_for(g.nv, 128), 128, 0, s>>>(g.nv, f.r_rp.get(), f.r_ent.get(), f.r_keys.get(),
+                                                              f.prp.get(), f.pci.get(), f.pw.get(), f.rp.get(),
+                                                              f.ci.get(), f.v.get(), f.dead.get(), g.rp.get(),
+                                                              g.ci.get(), g.v.get(), g.dead.get());
   else
-    gal_values_kernel<3><<<grid_for(g.nv, 128), 128, 0, s>>>(g.nv, rrp.get(), rent.get(), rkeys.get(), f.prp.get(),
-                                                              f.pci.get(), f.pw.get(), f.rp.get(), f.ci.get(),
-                                                              f.v.get(), f.dead.get(), g.rp.get(), g.ci.get(),
-                                                              g.v.get(), g.dead.get());
+    gal_values_kernel<3><<<grid_for(g.nv, 128), 128, 0, s>>>(g.nv, f.r_rp.get(), f.r_ent.get(), f.r_keys.get(),
+                                                              f.prp.get(), f.pci.get(), f.pw.get(), f.rp.get(),
+                                                              f.ci.get(), f.v.get(), f.dead.get(), g.rp.get(),
+                                                              g.ci.get(), g.v.get(), g.dead.get());
   check_launch("gal_values");
 }
 

@@ -1178,6 +1178,8 @@ struct EngineBase {
   virtual int solve(Ctx& c, const double* F, double* U, double tol, vasmg_stats* st) = 0;
   virtual void apply(Ctx& c, int op, int level, const double* x, double* y) = 0;
   virtual double time(Ctx& c, int which, int level, int reps, double* bytes) = 0;
+  // refill the engine's own copies of operator values (same structure)
+  virtual void refresh_values() = 0;
 };
 
 // Lanes per row: few enough that a CTA pass covers many rows (the sweeps are
@@ -1210,6 +1212,7 @@ struct Engine : EngineBase {
   DevBuf<double> U, r, p, q, part, hist, Fbuf, Ubuf;
   DevBuf<Scalars> sc;
   DevBuf<int32_t> sell_rows, sell_w, sell_ci;
+  DevBuf<int32_t> sell_order;     // level-0 rows sorted by length (SELL fill order)
   DevBuf<long long> sell_ptr;
   DevBuf<double> sell_v;
   i64 sell_real_entries = 0;
@@ -1342,13 +1345,36 @@ struct Engine : EngineBase {
     v.pg_u = pg_u[l].get();
   }
 
+  // New operator values on the same structure: the level-0 FP64 SELL copy
+  // and the split lower / upper parts of every level are refilled in place.
+  void refresh_values() override {
+    cudaStream_t s = c->stream;
+    SolveLevel& s0 = c->S[0];
+    const int nv = (int)s0.nv;
+    const long long nslices = ceil_div(nv, 32);
+    sell_fill_kernel<D><<<grid_for(nslices * 32, 256), 256, 0, s>>>(
+        sell_order.get(), s0.rp.get(), s0.ci.get(), s0.off64.get(), s0.nnz, s0.diag64.get(), nv, nslices,
+        sell_ptr.get(), sell_w.get(), cga.sell_tot, sell_ci.get(), sell_v.get(), sell_rows.get());
+    check_launch("sell_fill");
+    for (int l = 0; l + 1 < L; ++l) {
+      SolveLevel& sl = c->S[l];
+      if (sl.nv == 0) continue;
+      split_parts_kernel<S><<<grid_for(sl.nv, 256), 256, 0, s>>>(
+          sl.rp.get(), sl.sp.get(), sl.ci.get(), (const S*)off_ptr(sl), sl.nnz, D * D, (int)sl.nv, rpl_dev[l].get(),
+          rph_dev[l].get(), cil_dev[l].get(), offl_dev[l].get(), lv[l].nlo, cih_dev[l].get(), offh_dev[l].get(),
+          lv[l].nhi);
+      check_launch("split_parts");
+    }
+    VASMG_CUDA(cudaStreamSynchronize(s));
+  }
+
   void build_sell() {
     cudaStream_t s = c->stream;
     SolveLevel& s0 = c->S[0];
     const int nv = (int)s0.nv;
     DevBuf<u64> keys;
     keys.alloc(nv, s);
-    DevBuf<int32_t> rows;
+    DevBuf<int32_t>& rows = sell_order;
     rows.alloc(nv, s);
     sell_keys_kernel<<<grid_for(nv, 256), 256, 0, s>>>(s0.rp.get(), nv, keys.get(), rows.get());
     check_launch("sell_keys");
@@ -2047,6 +2073,8 @@ void setup_solver_state(Ctx& c) {
     else c.eng = new Engine<3, float, __nv_bfloat16>(c);
   }
 }
+
+void refresh_solver_values(Ctx& c) { c.eng->refresh_values(); }
 
 void destroy_solver_state(Ctx& c) {
   delete c.eng;

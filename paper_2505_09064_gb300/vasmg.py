@@ -33,7 +33,7 @@ EXPORTED = ["vasmg_default_options", "vasmg_setup", "vasmg_assemble_load", "vasm
             "vasmg_num_levels", "vasmg_level_info", "vasmg_export", "vasmg_apply", "vasmg_time_kernel",
             "vasmg_last_launch_count", "vasmg_destroy", "vasmg_error_string", "vasmg_last_error_detail",
             "vasmg_coarse_solve_noalloc", "vasmg_server_default_opts", "vasmg_server_create",
-            "vasmg_server_submit", "vasmg_server_poll", "vasmg_server_destroy"]
+            "vasmg_server_submit", "vasmg_server_poll", "vasmg_server_destroy", "vasmg_update_data"]
 
 OK, NOT_CONVERGED, PENDING = 0, 1, 2
 
@@ -102,6 +102,7 @@ def load():
     lib.vasmg_time_kernel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]
     lib.vasmg_coarse_solve_noalloc.argtypes = [P, P, P, P]
+    lib.vasmg_update_data.argtypes = [P, P, P, C.c_double, C.c_double, P]
     lib.vasmg_server_default_opts.argtypes = [C.POINTER(vasmg_server_opts)]
     lib.vasmg_server_create.argtypes = [C.POINTER(vasmg_server_opts), C.POINTER(P)]
     lib.vasmg_server_submit.argtypes = [P, C.POINTER(vasmg_problem), C.c_int32, P, P, C.POINTER(C.c_uint64)]
@@ -234,6 +235,16 @@ def vasmg_time_kernel(h, which: int, level: int = 0, reps: int = 10):
     return ms.value, nbytes.value
 
 
+def vasmg_update_data(h, lam=None, mu=None, lam_const=0.0, mu_const=0.0, dirichlet_values=None):
+    """New Lame parameters (per element, or constants) and / or Dirichlet
+    values on the same mesh and constrained dofs, reusing the hierarchy."""
+    lam = None if lam is None else np.ascontiguousarray(lam, dtype=np.float64)
+    mu = None if mu is None else np.ascontiguousarray(mu, dtype=np.float64)
+    dv = None if dirichlet_values is None else np.ascontiguousarray(dirichlet_values, dtype=np.float64)
+    _check(load().vasmg_update_data(h, _ptr(lam), _ptr(mu), float(lam_const), float(mu_const), _ptr(dv)),
+           "vasmg_update_data")
+
+
 def vasmg_coarse_solve_noalloc(h, b, x, stream=None):
     """x = A_L^{-1} b on the coarsest level without allocating (b, x: device
     tensors of dim * coarsest-vertices doubles, canonical order).  Enqueued on
@@ -298,6 +309,17 @@ class Solver:
 
     def apply(self, op, level, x, y):
         vasmg_apply(self.h, op, level, x, y)
+
+    def update(self, prob: dict):
+        """Take the material and Dirichlet values of `prob` (same mesh and
+        constrained dofs as at construction) without a new setup."""
+        ne = np.asarray(prob["elems"]).shape[0]
+        lam = np.broadcast_to(np.asarray(prob["lam"], dtype=np.float64), (ne,))
+        mu = np.broadcast_to(np.asarray(prob["mu"], dtype=np.float64), (ne,))
+        dv = prob.get("dirichlet_values")
+        if dv is None:
+            dv = np.zeros(np.asarray(prob.get("dirichlet_dofs", np.zeros(0))).size)
+        vasmg_update_data(self.h, lam, mu, 0.0, 0.0, dv)
 
 
 PRECISIONS_SERVER = {"fp64": 0, "fp32": 1, "bf16": 2}

@@ -12,27 +12,29 @@
 // Reductions are deterministic: every block writes one partial and the last
 // block to finish sums the partials in index order.
 //
-// V-cycle (precision V, operator values stored as S), for each level that is
-// not small enough for the tail, two self-scheduling launches:
-//   down  forward multicolour block Gauss-Seidel sweep from a zero initial
-//         guess, x_i = D_ii^{-1}(b_i - sum_{j of an earlier colour} A_ij x_j)
-//         (with a zero start the later colours contribute nothing, so only the
-//         "lower" part of each row is read); then the residual
-//         r_i = - sum_{j of a later colour} A_ij x_j (b_i - A_ii x_i - lower is
-//         exactly zero after the sweep); then the restriction b_{l+1} = P^T r
-//         (eq. (R)).  Pre-smoothing + residual read each block once.
-//   up    prolongation x_l += P x_{l+1} (masked at dead dofs), then one backward
-//         sweep (colours in reverse order) with full rows.
-// A launch is a pool of tiles (rows of one colour, residual rows, coarse rows)
-// claimed in order from an atomic counter.  A sweep tile waits only for the
-// tiles of earlier colours that hold its neighbours (per-tile flags stamped
-// with a launch epoch), so colours overlap and no launch or global barrier
-// separates them.  Every wait is bounded; a wait that gives up raises a
-// global abort flag and the solve returns VASMG_ERR_TIMEOUT.  The last block
-// to leave a launch resets its counters and advances the epoch.
+// V-cycle (precision V, operator values stored as S).  For each level with
+// more than TAIL_NV vertices, five launches:
+//   vdown     forward multicolour block Gauss-Seidel sweep from a zero initial
+//             guess, x_i = D_ii^{-1}(b_i - sum_{j of an earlier colour} A_ij x_j)
+//             (with a zero start the later colours contribute nothing, so only
+//             the "lower" part of each row is read, from its own arrays);
+//   residual  r_i = - sum_{j of a later colour} A_ij x_j (b_i - A_ii x_i - lower
+//             is exactly zero after the sweep), the "upper" part only;
+//   restrict  b_{l+1} = P^T r (eq. (R));
+//   prolong   x_l += P x_{l+1} (masked at dead dofs);
+//   vup       backward sweep (colours in reverse order) with full rows.
+// The two sweeps are cooperative launches with one CTA per region (a range of
+// spatial keys, one contiguous row range per colour).  A region runs its
+// colours in order; before a colour it waits until every neighbouring region
+// has published the stage it reads (64-bit epoch/stage words, release /
+// acquire at GPU scope).  Every wait is bounded; a wait that gives up raises a
+// global abort flag and the solve returns VASMG_ERR_TIMEOUT.  The last CTA to
+// leave a launch advances its epoch.  Residual, restriction and prolongation
+// have no dependencies within themselves and run as plain kernels.
 //
 // Levels with at most TAIL_NV vertices and the coarsest Cholesky solve run in
-// one thread-block-cluster kernel (hardware cluster barriers between phases).
+// one thread-block-cluster kernel (hardware cluster barriers between phases;
+// the smallest levels on CTA 0 alone with their vectors in shared memory).
 //
 // The whole solve is one CUDA graph with a conditional WHILE node (no host
 // round trip per iteration).
@@ -93,27 +95,6 @@ __device__ __forceinline__ void stx(V* p, V v) {
   else __stcg(p, v);
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ int ld_acquire_i(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void red_release_add(int* p, int v) {
-  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
   unsigned long long v;
@@ -292,10 +273,10 @@ struct RowPF {
   V di[D], bv[D];
 };
 
-// Row pass split in two.  row_prefetch loads everything that no other tile
-// writes during the launch (row range, the first NPF entries of this lane,
-// the diagonal inverse and b); row_finish, called once the tiles this row
-// depends on are done, gathers x and completes the row as row_pass does.
+// Row pass split in two.  row_prefetch loads everything that nothing writes
+// during the sweep (row range, the first NPF entries of this lane, the
+// diagonal inverse and b); row_finish, called once the rows this row depends
+// on are done, gathers x and completes the row as row_pass does.
 template <int D, int G, typename V, typename S, int MODE, typename L_t, bool LC = false, int NPF>
 __device__ __forceinline__ void row_prefetch(const L_t& L, int row, bool valid, int lane, RowPF<D, V, NPF>& st) {
   st.sg = RowSeg{0, 0, 0, 0};
@@ -1079,11 +1060,6 @@ __global__ void split_parts_kernel(const int* __restrict__ rp, const int* __rest
       for (int q = 0; q < dd; ++q) offh[(long long)q * nhi + d] = off[(long long)q * nnz + k];
     }
   }
-}
-
-__global__ void low32_e_kernel(const u64* __restrict__ k, i64 n, int* __restrict__ out) {
-  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
-    out[i] = (int)(k[i] & 0xffffffffull);
 }
 
 // SELL-32: rows sorted by length (longest first) inside windows of 1024 rows

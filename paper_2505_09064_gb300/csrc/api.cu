@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -286,12 +287,16 @@ int vasmg_solve_batch(int32_t k, const vasmg_handle* h, const double* const* F, 
     }
   }
   std::vector<int> rc(k, VASMG_OK);
+  // each solve's error detail, taken in the thread that ran it (the detail
+  // string is per thread) and handed to the caller's thread below
+  std::vector<std::string> detail(k);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return VASMG_ERR_CUDA;
   for (const auto& g : groups) {
     if (g.size() == 1) {
       const int32_t i = g[0];
       rc[i] = vasmg_solve(h[i], F[i], U[i], tol, st ? &st[i] : nullptr);
+      if (rc[i] < 0) detail[i] = g_last_error;
       continue;
     }
     std::vector<std::thread> th;
@@ -299,12 +304,16 @@ int vasmg_solve_batch(int32_t k, const vasmg_handle* h, const double* const* F, 
       th.emplace_back([&, i]() {
         cudaSetDevice(dev);
         rc[i] = vasmg_solve(h[i], F[i], U[i], tol, st ? &st[i] : nullptr);
+        if (rc[i] < 0) detail[i] = g_last_error;
       });
     for (auto& t : th) t.join();
   }
   int worst = VASMG_OK;
   for (int32_t i = 0; i < k; ++i) {
-    if (rc[i] < 0) return rc[i];
+    if (rc[i] < 0) {
+      g_last_error = "solve " + std::to_string(i) + " of the batch: " + detail[i];
+      return rc[i];
+    }
     worst = std::max(worst, rc[i]);
   }
   return worst;

@@ -3,7 +3,7 @@
 //
 // Pattern: the structural block product of P_s^T pattern(A_l) P_s plus the
 // diagonal (pairs (I, J) generated per fine vertex, radix sorted, made unique).
-// Values: one thread per coarse row I sums, in ascending fine index i and then
+// Values: one warp per coarse row I sums, in ascending fine index i and then
 // ascending block k of row i, w_iI (M A_l M)_ij w_jJ into its row -- a fixed
 // order, so the result is deterministic.  Coarse dofs whose masked column of
 // P is empty are dead and get identity rows.
@@ -57,67 +57,83 @@ __global__ void low32_i_kernel(const u64* __restrict__ k, i64 n, int32_t* __rest
     out[i] = (int32_t)(k[i] & 0xffffffffull);
 }
 
+// One warp per coarse row I.  The warp walks the items (t, k) of the row -- an
+// R entry t (fine vertex i, weight w_iI) and a block k of A_l's row i (column
+// j) -- in ascending t, then ascending k; the lanes split the (b, r, s) terms
+// of one item (b over the entries of P_j's row, (r, s) over the block), and
+// those all land on different scalars of row I, since the columns of one
+// row of P are distinct.  Every scalar thus receives its terms in the same
+// order as a single thread walking the row would add them.  The warp's
+// lanes then write the dead masks and identity rows.
 template <int D>
-__global__ void gal_values_kernel(i64 nc, const int32_t* __restrict__ rrp, const int32_t* __restrict__ rent,
-                                  const u64* __restrict__ rkeys, const int32_t* __restrict__ prp,
-                                  const int32_t* __restrict__ pci, const double* __restrict__ pw,
-                                  const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
-                                  const double* __restrict__ av, const uint8_t* __restrict__ fdead,
-                                  const int32_t* __restrict__ crp, const int32_t* __restrict__ cci,
-                                  double* __restrict__ cv, uint8_t* __restrict__ cdead) {
+__global__ void gal_values_kernel(
+    i64 nc, const int32_t* __restrict__ rrp, const int32_t* __restrict__ rent, const u64* __restrict__ rkeys,
+    const int32_t* __restrict__ prp, const int32_t* __restrict__ pci, const double* __restrict__ pw,
+    const int32_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
+    const uint8_t* __restrict__ fdead, const int32_t* __restrict__ crp, const int32_t* __restrict__ cci,
+    double* __restrict__ cv, uint8_t* __restrict__ cdead) {
   constexpr int DD = D * D;
-  for (i64 I = (i64)blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += (i64)gridDim.x * blockDim.x) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const i64 nwarps = (i64)gridDim.x * (blockDim.x >> 5);
+  for (i64 I = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < nc; I += nwarps) {
     const int32_t c0 = crp[I], c1 = crp[I + 1];
-    bool alive[D];
-#pragma unroll
-    for (int r = 0; r < D; ++r) alive[r] = false;
+    unsigned alive = 0;
     for (int32_t t = rrp[I]; t < rrp[I + 1]; ++t) {
       const i64 i = (i64)(rkeys[t] & 0xffffffffull);
       const double wI = pw[rent[t]];
-      bool fi[D];
+      unsigned fi = 0;
 #pragma unroll
-      for (int r = 0; r < D; ++r) {
-        fi[r] = !fdead[i * D + r];
-        alive[r] = alive[r] || fi[r];
-      }
-      for (int32_t k = arp[i]; k < arp[i + 1]; ++k) {
-        const i64 j = aci[k];
-        const double* B = av + (i64)k * DD;
-        bool fj[D];
+      for (int r = 0; r < D; ++r) fi |= fdead[i * D + r] ? 0u : 1u << r;
+      alive |= fi;
+      const int32_t k0 = arp[i], k1 = arp[i + 1];
+      for (int32_t kb = k0; kb < k1; kb += 32) {
+        const int nk = min(32, k1 - kb);
+        // the lanes fetch the column data of up to 32 items at once
+        int32_t p0l = 0, p1l = 0;
+        unsigned fjl = 0;
+        if (lane < nk) {
+          const i64 j = aci[kb + lane];
+          p0l = prp[j];
+          p1l = prp[j + 1];
 #pragma unroll
-        for (int s = 0; s < D; ++s) fj[s] = !fdead[j * D + s];
-        for (int32_t b = prp[j]; b < prp[j + 1]; ++b) {
-          const int32_t J = pci[b];
-          const double wJ = pw[b];
-          int32_t lo = c0, hi = c1;
-          while (lo < hi) {
-            const int32_t mid = (lo + hi) >> 1;
-            if (cci[mid] < J) lo = mid + 1; else hi = mid;
-          }
-          double* C = cv + (i64)lo * DD;
-#pragma unroll
-          for (int r = 0; r < D; ++r) {
-            if (!fi[r]) continue;
-#pragma unroll
-            for (int s = 0; s < D; ++s) {
-              if (!fj[s]) continue;
-              C[r * D + s] = __dadd_rn(C[r * D + s], __dmul_rn(__dmul_rn(wI, B[r * D + s]), wJ));
+          for (int s = 0; s < D; ++s) fjl |= fdead[j * D + s] ? 0u : 1u << s;
+        }
+        for (int q = 0; q < nk; ++q) {
+          const int32_t p0 = __shfl_sync(FULL, p0l, q), p1 = __shfl_sync(FULL, p1l, q);
+          const unsigned fj = __shfl_sync(FULL, fjl, q);
+          const double* B = av + (i64)(kb + q) * DD;
+          const int nterm = (p1 - p0) * DD;
+          for (int e = lane; e < nterm; e += 32) {
+            const int bq = e / DD, rs = e - bq * DD, r = rs / D, sc = rs - r * D;
+            if (!((fi >> r) & 1u) || !((fj >> sc) & 1u)) continue;
+            const int32_t J = pci[p0 + bq];
+            const double wJ = pw[p0 + bq];
+            int32_t lo = c0, hi = c1;
+            while (lo < hi) {
+              const int32_t mid = (lo + hi) >> 1;
+              if (cci[mid] < J) lo = mid + 1; else hi = mid;
             }
+            double* C = cv + (i64)lo * DD + rs;
+            *C = __dadd_rn(*C, __dmul_rn(__dmul_rn(wI, B[rs]), wJ));
           }
+          // the next item may add to a scalar another lane just wrote
+          __syncwarp();
         }
       }
     }
     // dead coarse dofs -> identity rows (their masked column of P is empty)
-    int32_t lo = c0, hi = c1;
-    while (lo < hi) {
-      const int32_t mid = (lo + hi) >> 1;
-      if (cci[mid] < (int32_t)I) lo = mid + 1; else hi = mid;
+    if (lane < D) {
+      int32_t lo = c0, hi = c1;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (cci[mid] < (int32_t)I) lo = mid + 1; else hi = mid;
+      }
+      const bool al = (alive >> lane) & 1u;
+      cdead[I * D + lane] = al ? 0 : 1;
+      if (!al) cv[(i64)lo * DD + lane * D + lane] = 1.0;
     }
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      cdead[I * D + r] = alive[r] ? 0 : 1;
-      if (!alive[r]) cv[(i64)lo * DD + r * D + r] = 1.0;
-    }
+    __syncwarp();
   }
 }
 
@@ -173,12 +189,12 @@ void galerkin_values(Ctx& c, int l) {
   g.v.zero();
   if (g.dead.n != g.nv * d) g.dead.alloc(g.nv * d, s);
   if (d == 2)
-    gal_values_kernel<2><<<grid_for(g.nv, 128), 128, 0, s>>>(g.nv, f.r_rp.get(), f.r_ent.get(), f.r_keys.get(),
+    gal_values_kernel<2><<<grid_for(g.nv * 32, 256), 256, 0, s>>>(g.nv, f.r_rp.get(), f.r_ent.get(), f.r_keys.get(),
                                                               f.prp.get(), f.pci.get(), f.pw.get(), f.rp.get(),
                                                               f.ci.get(), f.v.get(), f.dead.get(), g.rp.get(),
                                                               g.ci.get(), g.v.get(), g.dead.get());
   else
-    gal_values_kernel<3><<<grid_for(g.nv, 128), 128, 0, s>>>(g.nv, f.r_rp.get(), f.r_ent.get(), f.r_keys.get(),
+    gal_values_kernel<3><<<grid_for(g.nv * 32, 256), 256, 0, s>>>(g.nv, f.r_rp.get(), f.r_ent.get(), f.r_keys.get(),
                                                               f.prp.get(), f.pci.get(), f.pw.get(), f.rp.get(),
                                                               f.ci.get(), f.v.get(), f.dead.get(), g.rp.get(),
                                                               g.ci.get(), g.v.get(), g.dead.get());

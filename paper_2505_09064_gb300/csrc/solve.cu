@@ -53,6 +53,11 @@ constexpr int TAIL_G = 8;
 template <int D>
 constexpr int tail_g() { return D == 2 ? TAIL_G : 32; }
 constexpr int ONE_CTA_NV = 1200;  // tail levels this small run on one CTA
+// Dynamic shared memory the tail kernel is configured for.  The limit is an
+// attribute of the kernel function, shared by every handle in the process, so
+// every engine sets the same value once instead of its own size: a handle
+// with a smaller tail would otherwise lower the limit under another one.
+constexpr int TAIL_SMEM_MAX = 200 * 1024;
 constexpr int MAX_LEVELS = 40;
 constexpr int CG_THREADS = 256;
 constexpr int DF_THREADS = 256;
@@ -1174,7 +1179,6 @@ struct Engine : EngineBase {
   int lt = 0;      // first tail level
   int nct = 1;     // CTAs in the tail cluster
   int sms_ = 1;    // SMs of the device
-  size_t tail_smem_set = 0;  // dynamic shared memory the tail kernel is configured for
   std::vector<LV<V>> lv;
   std::vector<int> G;
   std::vector<DevBuf<int32_t>> cs_dev, rs_dev, nb_rp, nb;
@@ -1477,6 +1481,7 @@ struct Engine : EngineBase {
       c->ctas_used = std::max(c->ctas_used, R);
       c->cta_capacity = c->cta_capacity ? std::min<int>(c->cta_capacity, (int)cap) : (int)cap;
     }
+    VASMG_CUDA(cudaFuncSetAttribute(tail_kernel<D, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM_MAX));
     // tail cluster size: as many CTAs (<= 16) as the work of the tail levels warrants
     {
       i64 work = 0;
@@ -1630,11 +1635,7 @@ struct Engine : EngineBase {
       smem += 3 * sizeof(V) * (size_t)c->S[l].nv * D;
       smem = (smem + 15) / 16 * 16;
     }
-    if (smem > tail_smem_set) {
-      VASMG_CHECK(smem <= 200 * 1024, VASMG_ERR_UNSUPPORTED, "tail levels too large for shared memory");
-      VASMG_CUDA(cudaFuncSetAttribute(tail_kernel<D, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      tail_smem_set = smem;
-    }
+    VASMG_CHECK(smem <= (size_t)TAIL_SMEM_MAX, VASMG_ERR_UNSUPPORTED, "tail levels too large for shared memory");
     for (int l = 0; l < L; ++l) {
       const LV<V>& v = lv[l];
       TL<V>& t = ta.lv[l];
@@ -1784,7 +1785,16 @@ struct Engine : EngineBase {
     cudaGraph_t bg = nullptr;
     launch_counter = 0;
     VASMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    body(s);
+    try {
+      body(s);
+    } catch (...) {
+      // leave the stream out of capture mode before reporting the error
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(s, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      cudaGetLastError();
+      throw;
+    }
     VASMG_CUDA(cudaStreamEndCapture(s, &bg));
     launches_body = launch_counter;
     VASMG_CUDA(cudaGraphInstantiate(&exec_body, bg, 0));

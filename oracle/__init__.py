@@ -4,8 +4,10 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The library in
 ``paper_2505_09064_gb300`` never does, and this package never imports the
 library: the two share no code.  The arithmetic lives in ``vasmg_oracle.cpp``
-(plain single-threaded C++, IEEE FP64, no FMA contraction); this module only
-compiles it and marshals arrays through ctypes.
+(plain C++, IEEE FP64, no FMA contraction); this module only compiles it and
+marshals arrays through ctypes.  ``Oracle(prob, threads=k)`` with k > 1 loads a
+second build of the same file with OpenMP, whose independent row loops run on
+k threads and give the same bits as the single-threaded build.
 """
 from __future__ import annotations
 
@@ -19,30 +21,33 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vasmg_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 # export selectors (match the enum in vasmg_oracle.cpp)
 MORTON, LEAF, LEAF_SORTED, CELLS, LATTICE, P_RP, P_CI, P_W, A_RP, A_CI, A_V, DEAD, COLOUR, DINV, BOX, LIFT, VOL = range(17)
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so next to its source (plain g++, IEEE semantics)."""
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile liboracle.so (or, parallel=True, liboracle_omp.so: the same
+    source with -fopenmp) next to its source (plain g++, IEEE semantics)."""
+    out = _LIB_OMP if parallel else _LIB
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                   _SRC, "-o", tmp]
-            subprocess.run(cmd, check=True)
-            os.replace(tmp, _LIB)
-    return _LIB
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+            tmp = out + f".tmp{os.getpid()}"
+            cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+            if parallel:
+                cmd.append("-fopenmp")
+            subprocess.run(cmd + [_SRC, "-o", tmp], check=True)
+            os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        build()
-        lib = C.CDLL(_LIB)
+def _load(parallel: bool = False):
+    lib = _libs.get(parallel)
+    if lib is None:
+        lib = C.CDLL(build(parallel=parallel))
         P = C.c_void_p
         lib.or_setup.argtypes = [C.c_int, C.c_int64, P, C.c_int64, P, P, P, C.c_int64, P, P, C.c_int, C.c_int64,
                                  P, C.POINTER(C.c_void_p)]
@@ -69,8 +74,10 @@ def _load():
                                  C.c_int, C.c_int]
         lib.or_splitmix64.argtypes = [C.c_uint64]
         lib.or_splitmix64.restype = C.c_uint64
-        _lib = lib
-    return _lib
+        lib.or_set_threads.argtypes = [C.c_int]
+        lib.or_set_threads.restype = C.c_int
+        _libs[parallel] = lib
+    return lib
 
 
 def _ptr(a):
@@ -81,10 +88,13 @@ class Oracle:
     """Setup + solve of V-ASMG-PCG on the CPU in FP64 (one hierarchy)."""
 
     def __init__(self, prob: dict, threshold: int = 0, coarse_max_dofs: int = 0, insertion_order=None,
-                 fine_only: bool = False):
+                 fine_only: bool = False, threads: int = 1):
         """fine_only: assembly, Dirichlet rows and keys only (apply_A(0), the
-        load, keys and sorted-key leaves work; nothing of the hierarchy)."""
-        lib = _load()
+        load, keys and sorted-key leaves work; nothing of the hierarchy).
+        threads > 1: the OpenMP build, its row loops on that many threads
+        (self.threads is the count it reports)."""
+        lib = _load(parallel=threads > 1)
+        self.threads = int(lib.or_set_threads(int(threads))) if threads > 1 else 1
         self.dim = int(prob["dim"])
         self.coords = np.ascontiguousarray(prob["coords"], dtype=np.float64)
         self.elems = np.ascontiguousarray(prob["elems"], dtype=np.int32)

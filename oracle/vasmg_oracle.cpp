@@ -1,12 +1,16 @@
 // V-ASMG-PCG oracle (arXiv 2505.09064) -- TEST INFRASTRUCTURE ONLY.
 //
-// A plain, slow, single-threaded FP64 CPU implementation of what the solve path
-// computes.  Only the test-suite, the smoke check and the CPU-baseline leg of
+// A plain, slow FP64 CPU implementation of what the solve path computes,
+// single-threaded as built by default.  Only the test-suite, the smoke check and the CPU-baseline leg of
 // the benchmark may load it; the library never does.  It shares no code with
 // the CUDA path: every step is written here from the paper's description, in
 // the paper's order, with no blocking, fusion or reordering.  Build flags keep
 // IEEE semantics (-O2 -ffp-contract=off) so the geometric steps round exactly
-// as written.
+// as written.  A second build of this same file with -fopenmp (the parallel
+// CPU line of the benchmark) runs three kinds of independent row loops on
+// all host cores: the rows of one colour in a sweep, the rows of y = A x, and
+// the fine rows of the prolongation.  No reduction is split, and every row
+// keeps its own order of additions, so both builds give the same bits.
 //
 // Steps (paper section / equation / algorithm):
 //   assembly            Sec. 2, the 2x2 block form of A and F (P1 elements),
@@ -40,6 +44,9 @@
 #include <set>
 #include <utility>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -104,8 +111,11 @@ BSR pattern_from_pairs(int d, i64 n, std::vector<std::pair<int32_t, int32_t>>& p
 }
 
 // y = A x (full vector, dof = vertex*d + component).
+// The rows are independent; the parallel build of this file splits them over
+// threads (each row's sum keeps its order, so the result is the same).
 void bsr_apply(const BSR& A, const double* x, double* y) {
   const int d = A.d;
+#pragma omp parallel for schedule(static)
   for (i64 i = 0; i < A.n; ++i) {
     for (int a = 0; a < d; ++a) y[i * d + a] = 0.0;
     for (i64 k = A.rp[i]; k < A.rp[i + 1]; ++k) {
@@ -767,11 +777,16 @@ void solve_coarsest(const Oracle& o, const double* b, double* x) {
 
 // One multicolour block Gauss-Seidel sweep: for each colour in turn, every
 // vertex i of that colour sets x_i = D_ii^{-1} (b_i - sum_{j != i} A_ij x_j).
+// The vertices of one colour are never neighbours, so within a colour the
+// updates are independent (the parallel build splits them over threads).
 void gs_sweep(const Oracle& o, const Level& lv, const double* b, double* x, bool forward) {
   const int d = o.dim;
   for (int cc = 0; cc < lv.ncol; ++cc) {
     const int c = forward ? cc : lv.ncol - 1 - cc;
-    for (int32_t i : lv.by_colour[c]) {
+    const std::vector<int32_t>& vs = lv.by_colour[c];
+#pragma omp parallel for schedule(static)
+    for (i64 t = 0; t < (i64)vs.size(); ++t) {
+      const int32_t i = vs[t];
       double r[3];
       for (int a = 0; a < d; ++a) r[a] = b[(i64)i * d + a];
       for (i64 k = lv.A.rp[i]; k < lv.A.rp[i + 1]; ++k) {
@@ -837,6 +852,7 @@ void restrict_to(const Oracle& o, const Level& fine, const Level& coarse, const 
 
 void prolong_add(const Oracle& o, const Level& fine, const double* ec, double* x) {
   const int d = o.dim;
+#pragma omp parallel for schedule(static)
   for (i64 i = 0; i < fine.nv; ++i)
     for (i64 a = fine.P.rp[i]; a < fine.P.rp[i + 1]; ++a)
       for (int c = 0; c < d; ++c)
@@ -1177,6 +1193,18 @@ int or_apply_A(const oracle_t* o, int l, const double* x, double* y) {
 // One multicolour GS sweep on level l, in place on x.
 // Select the smoother of the V-cycle and of or_gs_sweep: 0 multicolour
 // point-block GS (the GPU path's), 1 scalar lexicographic GS (the paper's).
+// Threads of the parallel build (returns the count in use); the default
+// build runs on one thread and returns 1.
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 int or_set_smoother(oracle_t* o, int smoother) {
   if (!o || smoother < 0 || smoother > 1) return -1;
   o->smoother = smoother;

@@ -297,8 +297,9 @@ def ours(args):
     n = prob["coords"].shape[0] * prob["dim"]
     nfree = n - prob["dirichlet_dofs"].size
 
-    def run_solver(precision):
-        s = vasmg.Solver(prob, precision=precision, stream=stream, use_graph=not args.no_graph)
+    def run_solver(precision, threshold=0):
+        s = vasmg.Solver(prob, precision=precision, stream=stream, use_graph=not args.no_graph,
+                         threshold=threshold)
         F = torch.zeros(n, dtype=torch.float64, device=dev)
         s.assemble_load(prob["body_force"], F)
         U = torch.zeros_like(F)
@@ -385,6 +386,17 @@ def ours(args):
         fp64 = {"value": nfree * sum(it64) / (ms64 / 1e3) / 1e6, "iterations": it64[0],
                 "ms_per_solve": ms64 / len(it64)}
         s64.close()
+    # the same solve with a coarser region tree (leaf threshold 8, not the
+    # paper's 4 in 2D): fewer, sparser coarse levels for a few more iterations
+    variants = None
+    if args.workload.startswith("square") and world == 1:
+        sT, FT, UT = run_solver(args.precision, threshold=8)
+        msT, itT, _, _ = timed(sT, FT, UT, max(1, args.steps))
+        nbT = [vasmg.vasmg_level_info(sT.h, l)[1] for l in range(vasmg.vasmg_num_levels(sT.h))]
+        variants = {"leaf_threshold_8": {"value": nfree * sum(itT) / (msT / 1e3) / 1e6, "unit": "MDOF*iter/s",
+                                         "iterations": itT[0], "ms_per_solve": msT / len(itT),
+                                         "op_complexity": sum(nbT) / nbT[0], "levels": len(nbT)}}
+        sT.close()
     serving = None
     if not args.no_serving:
         serving = serving_run(stream)
@@ -409,7 +421,7 @@ def ours(args):
                                       for k, v in kernels.items()},
                          "vcycle": {"ms": vc_ms, "bytes": vc_bytes, "gbs": vc_bytes / (vc_ms / 1e3) / 1e9}},
             "e2e": {"value": e2e, "unit": "MDOF*iter/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
-            "gpu_launches": launches, "clocks": clk, "fp64_path": fp64, "serving": serving}
+            "gpu_launches": launches, "clocks": clk, "fp64_path": fp64, "variants": variants, "serving": serving}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         vals, nf, _ = cpu_oracle_run(SAMPLE_N, 2)
         v = vals[-1]

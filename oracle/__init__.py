@@ -74,6 +74,10 @@ def _load(parallel: bool = False):
                                  C.c_int, C.c_int]
         lib.or_splitmix64.argtypes = [C.c_uint64]
         lib.or_splitmix64.restype = C.c_uint64
+        lib.or_set_cycle.argtypes = [P, C.c_int, C.c_int]
+        lib.or_set_cycle.restype = C.c_int
+        lib.or_precondition.argtypes = [P, P, P]
+        lib.or_precondition.restype = C.c_int
         lib.or_set_threads.argtypes = [C.c_int]
         lib.or_set_threads.restype = C.c_int
         _libs[parallel] = lib
@@ -200,6 +204,20 @@ class Oracle:
         rc = self._lib.or_set_smoother(self._h, {"multicolour": 0, "lexicographic": 1}[smoother])
         if rc != 0:
             raise RuntimeError("or_set_smoother failed")
+
+    def set_cycle(self, gamma: int = 1, additive: bool = False):
+        """gamma coarse corrections per level (1: V-cycle, 2: W-cycle);
+        additive: the preconditioner B_h = S_h + Pi B_0 Pi^T (Sec. 4), with
+        S_h symmetric GS and B_0 the cycle on level 1."""
+        if self._lib.or_set_cycle(self._h, int(gamma), 1 if additive else 0) != 0:
+            raise RuntimeError("or_set_cycle failed")
+
+    def precondition(self, r):
+        """z = B r, the preconditioner PCG applies (current cycle variant)."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.empty_like(r)
+        self._lib.or_precondition(self._h, _ptr(r), _ptr(z))
+        return z
 
     def gs_sweep(self, l: int, b, x, forward=True):
         b = np.ascontiguousarray(b, dtype=np.float64)

@@ -26,7 +26,9 @@
 //   Galerkin            eq. (R), eq. (Ac)
 //   smoother            Sec. 2.1 / Alg. 1 as multicolour point-block GS
 //   coarsest solve      Sec. 3, Step 2.3 (Cholesky)
-//   V-cycle             Alg. 3 applied recursively, zero initial guess
+//   V-cycle             Alg. 3 applied recursively, zero initial guess;
+//                       W-cycle (Fig. 2) and the additive form
+//                       B_h = S_h + Pi B_0 Pi^T (Sec. 4) as comparators
 //   PCG                 Alg. 2, stop rule of Sec. 5 item (3)
 //
 // Parity status: every function here is pinned by the CPU test-suite
@@ -195,6 +197,8 @@ struct Level {
 struct Oracle {
   int dim = 2, K = 31, T = 4;
   int smoother = 0;               // 0: multicolour point-block GS, 1: scalar lexicographic GS
+  int gamma = 1;                  // coarse corrections per level: 1 = V-cycle, 2 = W-cycle (Fig. 2)
+  int additive = 0;               // 1: B_h = S_h + Pi B_0 Pi^T at the fine level (Sec. 4)
   i64 nv = 0, ne = 0, coarse_max_dofs = 0;
   std::vector<double> X;
   std::vector<int32_t> E;
@@ -862,6 +866,9 @@ void prolong_add(const Oracle& o, const Level& fine, const double* ec, double* x
 // Alg. 3 (two-level V-cycle) used recursively, as the preconditioner:
 // zero initial guess, n1 pre-smoothing and n2 post-smoothing sweeps with the
 // post-smoothing sweeps in reverse order, direct solve on the coarsest level.
+// With o.gamma = 2 it is the W-cycle of Fig. 2: the coarse problem
+// A_{l+1} e = R r is approximated by gamma cycles from e = 0, each on the
+// current coarse residual (the coarsest level is solved once, exactly).
 void vcycle(const Oracle& o, size_t l, const double* b, double* x, int n1, int n2) {
   const Level& lv = o.L[l];
   const int d = o.dim;
@@ -876,11 +883,51 @@ void vcycle(const Oracle& o, size_t l, const double* b, double* x, int n1, int n
   bsr_apply(lv.A, x, r.data());
   for (i64 i = 0; i < n; ++i) r[i] = b[i] - r[i];
   const Level& cv = o.L[l + 1];
-  std::vector<double> bc(cv.nv * d), ec(cv.nv * d);
+  const i64 nc = cv.nv * d;
+  std::vector<double> bc(nc), ec(nc);
   restrict_to(o, lv, cv, r.data(), bc.data());
   vcycle(o, l + 1, bc.data(), ec.data(), n1, n2);
+  const int reps = l + 2 == o.L.size() ? 1 : o.gamma;
+  for (int rep = 1; rep < reps; ++rep) {
+    std::vector<double> rc(nc), dc(nc);
+    bsr_apply(cv.A, ec.data(), rc.data());
+    for (i64 i = 0; i < nc; ++i) rc[i] = bc[i] - rc[i];
+    vcycle(o, l + 1, rc.data(), dc.data(), n1, n2);
+    for (i64 i = 0; i < nc; ++i) ec[i] += dc[i];
+  }
   prolong_add(o, lv, ec.data(), x);
   for (int s = 0; s < n2; ++s) smooth(o, lv, b, x, false);
+}
+
+// The additive form of Sec. 4, B_h = S_h + Pi B_0 Pi^T, at the fine level:
+// S_h is the symmetric Gauss-Seidel smoother (n1 forward then n2 backward
+// sweeps from zero), Pi = P_0, and B_0 is the cycle above on level 1 (the
+// exact inverse when level 1 is the coarsest).  The two terms are summed.
+void additive_precond(const Oracle& o, const double* r, double* z, int n1, int n2) {
+  const Level& lv = o.L[0];
+  const int d = o.dim;
+  const i64 n = lv.nv * d;
+  if (o.L.size() == 1) {
+    solve_coarsest(o, r, z);
+    return;
+  }
+  for (i64 i = 0; i < n; ++i) z[i] = 0.0;
+  for (int s = 0; s < n1; ++s) smooth(o, lv, r, z, true);
+  for (int s = 0; s < n2; ++s) smooth(o, lv, r, z, false);
+  const Level& cv = o.L[1];
+  std::vector<double> bc(cv.nv * d), ec(cv.nv * d);
+  restrict_to(o, lv, cv, r, bc.data());
+  vcycle(o, 1, bc.data(), ec.data(), n1, n2);
+  prolong_add(o, lv, ec.data(), z);
+}
+
+// The preconditioner PCG applies: the cycle from the fine level, or the
+// additive form.
+void apply_preconditioner(const Oracle& o, const double* r, double* z) {
+  if (o.additive)
+    additive_precond(o, r, z, 1, 1);
+  else
+    vcycle(o, 0, r, z, 1, 1);
 }
 
 // ---------------------------------------------------------------- setup driver
@@ -957,7 +1004,7 @@ int pcg(const Oracle& o, const double* Fin, double* U, double tol, int max_iters
   }
   auto applyM = [&](const std::vector<double>& rr, std::vector<double>& zz) {
     if (precondition)
-      vcycle(o, 0, rr.data(), zz.data(), 1, 1);
+      apply_preconditioner(o, rr.data(), zz.data());
     else
       zz = rr;
   };
@@ -1221,6 +1268,22 @@ int or_gs_sweep(const oracle_t* o, int l, const double* b, double* x, int forwar
 int or_vcycle(const oracle_t* o, int l, const double* b, double* x) {
   if (l < 0 || l >= (int)o->L.size()) return -1;
   vcycle(*o, (size_t)l, b, x, 1, 1);
+  return 0;
+}
+
+// Cycle variant: gamma >= 1 coarse corrections per level (1 = V, 2 = W);
+// additive = 1 makes the preconditioner B_h = S_h + Pi B_0 Pi^T.
+int or_set_cycle(oracle_t* o, int gamma, int additive) {
+  if (!o || gamma < 1 || gamma > 8 || additive < 0 || additive > 1) return -1;
+  o->gamma = gamma;
+  o->additive = additive;
+  return 0;
+}
+
+// z = B r with the preconditioner PCG uses (cycle variant included).
+int or_precondition(const oracle_t* o, const double* r, double* z) {
+  if (!o) return -1;
+  apply_preconditioner(*o, r, z);
   return 0;
 }
 

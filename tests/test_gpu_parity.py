@@ -312,6 +312,33 @@ def test_theorem_3_2_on_device(built, dim, k):
         assert np.array_equal(s.export(vasmg.EXPORT_P_CI, l, np.int32), o.prolongation(l)[1])
 
 
+@pytest.mark.parametrize("T", [4, 8, 9])
+@pytest.mark.parametrize("dim,n", [(2, 40), (3, 9)])
+def test_threshold_sweep_matches_oracle(built, dim, n, T):
+    """Leaf threshold T in {4, 8, 9} (the paper's 4 and two coarser trees):
+    the same hierarchy as the oracle, bit for bit, and the same FP64 solve."""
+    p = meshgen.make_problem(None, dim=dim, n=n, jitter=0.2 if dim == 2 else 0.15, seed=60 + n, nu=0.35)
+    o = oracle.Oracle(p, threshold=T)
+    s = vasmg.Solver(p, stream=torch.cuda.current_stream().cuda_stream, threshold=T)
+    try:
+        assert s.num_levels == o.num_levels
+        for l in range(o.num_levels - 1):
+            orp, oci, ow = o.prolongation(l)
+            assert np.array_equal(s.export(vasmg.EXPORT_P_RP, l, np.int64), orp)
+            assert np.array_equal(s.export(vasmg.EXPORT_P_CI, l, np.int32), oci)
+            assert np.array_equal(s.export(vasmg.EXPORT_P_W, l, np.float64), ow)
+        for l in range(o.num_levels):
+            assert np.array_equal(s.export(vasmg.EXPORT_A_CI, l, np.int32), o.operator(l)[1])
+            assert np.array_equal(s.export(vasmg.EXPORT_COLOUR, l, np.int32), o.colours(l))
+        F = o.assemble_load(p["body_force"])
+        U_ref, it_ref, _, _, _ = o.solve(F, tol=1e-6)
+        U = np.zeros_like(F)
+        rc, st, _ = s.solve(F, U, tol=1e-6)
+        assert rc == 0 and abs(st.iterations - it_ref) <= 1 and _rel(U, U_ref) <= 1e-10
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_random_problems(built, seed):
     p = meshgen.random_problem(seed)

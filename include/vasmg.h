@@ -92,6 +92,15 @@ typedef struct {
                                   many, so that handles whose caps add up to at
                                   most the device's capacity can solve
                                   concurrently (vasmg_solve_batch, the server) */
+  int32_t dense_coarse;        /* FP32-vector modes only.  1 (default): the
+                                  V-cycle from the first small level k whose
+                                  order n_k fits (n_k^2 <= tail CTAs * 640^2)
+                                  down to the coarsest is precomputed at setup
+                                  as one dense n_k x n_k matrix (the cycle
+                                  applied to the unit vectors) and applied as
+                                  one matrix-vector product: the same linear
+                                  operator up to FP32 rounding.  0: run the
+                                  recursion.  Ignored by VASMG_FP64. */
   void* stream;                /* cudaStream_t used for all device work */
 } vasmg_options;
 
@@ -238,7 +247,8 @@ enum {
   VASMG_EXPORT_DINV = 13,        /* f64[nv_l*dim*dim] inverses of the diagonal blocks */
   VASMG_EXPORT_BOX = 14,         /* f64[2] bounding square (m, M) */
   VASMG_EXPORT_LIFT = 15,        /* f64[n] A u_D of the Dirichlet data */
-  VASMG_EXPORT_VOL = 16          /* f64[n_elements] element measures */
+  VASMG_EXPORT_VOL = 16,         /* f64[n_elements] element measures */
+  VASMG_EXPORT_DENSE = 17        /* i64[2] (k, n_k) of the dense level, (-1, 0) if none (level ignored) */
 };
 
 /* Copy an exported array to host buffer buf (NULL: only report the size).

@@ -100,6 +100,7 @@ int vasmg_default_options(int dim, vasmg_options* out) {
   out->coarse_max_dofs = 0;
   out->max_iters = 1000;
   out->use_graph = 1;
+  out->dense_coarse = 1;
   out->stream = nullptr;
   return VASMG_OK;
 }
@@ -117,7 +118,8 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   if (opt) o = *opt; else vasmg_default_options(d, &o);
   if (o.n_pre != 1 || o.n_post != 1) return VASMG_ERR_UNSUPPORTED;
   if (o.precision < VASMG_FP64 || o.precision > VASMG_FP32_VCYCLE_BF16_SMOOTH) return VASMG_ERR_INVALID_ARG;
-  if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096 || o.max_iters <= 0 || o.max_ctas < 0)
+  if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096 || o.max_iters <= 0 || o.max_ctas < 0 ||
+      o.dense_coarse < 0 || o.dense_coarse > 1)
     return VASMG_ERR_INVALID_ARG;
   vasmg_ctx* h = new vasmg_ctx();
   struct Guard {
@@ -137,6 +139,7 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   c.max_iters = o.max_iters;
   c.use_graph = o.use_graph;
   c.max_ctas = o.max_ctas > 0 ? o.max_ctas : 0;
+  c.dense_coarse = o.dense_coarse;
   c.coarse_max_dofs = o.coarse_max_dofs;
   c.user_stream = (cudaStream_t)o.stream;
   VASMG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
@@ -376,6 +379,13 @@ int vasmg_export(vasmg_handle h, int32_t what, int32_t level, void* buf, int64_t
     }
     case VASMG_EXPORT_LIFT: dev(c.lift.get(), (size_t)c.n * 8); break;
     case VASMG_EXPORT_VOL: dev(c.vol.get(), (size_t)c.ne * 8); break;
+    case VASMG_EXPORT_DENSE: {
+      int kd = -1, dn = 0;
+      dense_level_info(c, &kd, &dn);
+      int64_t v[2] = {kd, dn};
+      put(v, 16);
+      break;
+    }
     default: {
       VASMG_CHECK(lvl_ok, VASMG_ERR_INVALID_ARG, "level out of range");
       CanonLevel& L = c.C[level];

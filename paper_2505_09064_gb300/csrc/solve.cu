@@ -59,6 +59,10 @@ constexpr int ONE_CTA_NV = 1200;  // tail levels this small run on one CTA
 // with a smaller tail would otherwise lower the limit under another one.
 constexpr int TAIL_SMEM_MAX = 200 * 1024;
 constexpr int MAX_LEVELS = 40;
+// The dense level (FP32 vectors only): the first level of the one-CTA tail
+// part whose order n satisfies n^2 <= (CTAs of the tail cluster) *
+// DENSE_ROWS_PER_CTA^2; the cluster reads M once per V-cycle.
+constexpr int DENSE_ROWS_PER_CTA = 640;
 constexpr int CG_THREADS = 256;
 constexpr int DF_THREADS = 256;
 constexpr int REGION_MIN_ROWS = 32;  // fewest rows a sweep region is given
@@ -648,6 +652,11 @@ template <typename V>
 struct TailArgs {
   int l0, L;                     // levels l0..L handled here, L = coarsest
   int ls;                        // levels ls..L run on CTA 0 alone
+  int kd;                        // dense level (ls <= kd <= L) or -1: x_kd = M b_kd replaces levels kd..L
+  int dn;                        // n_kd = nv_kd * d, the order of M
+  int dld;                       // row stride of M: dn rounded up to a multiple of 4 (zero padding)
+  int dsoff;                     // shared-memory offset (in V, 16-byte aligned) of b_kd staged for M b_kd
+  const V* dm;                   // M, row-major dn x dld: the V-cycle from level kd as a matrix
   int soff[MAX_LEVELS];          // shared-memory offset (in V) of x_l, b_l, r_l for l >= ls
   TL<V> lv[MAX_LEVELS];
   CoarseArgs co;
@@ -724,23 +733,15 @@ __device__ __forceinline__ TL<V> shared_level(const TailArgs<V>& A, int l, V* sm
   return L;
 }
 
-// Levels ls..L of the V-cycle on one CTA: phases separated by CTA barriers,
-// every vector in shared memory (only b_ls comes in and x_ls goes out), the
-// operators read through L1.
+// Levels lfrom..lto-1 of the one-CTA part, going down: forward sweep from
+// zero, residual, restriction into level l+1's b; every vector in shared
+// memory, the operators read through L1.
 template <int D, typename V, typename S>
-__device__ void tail_one_cta(const TailArgs<V>& A) {
+__device__ __forceinline__ void one_cta_down(const TailArgs<V>& A, V* sm, int lfrom, int lto) {
   constexpr int G = tail_g<D>();
-  extern __shared__ __align__(16) unsigned char tail_smem[];
-  V* sm = reinterpret_cast<V*>(tail_smem);
   const int ng = blockDim.x / G, g = (int)threadIdx.x / G, lane = threadIdx.x & (G - 1);
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int ls = A.ls, Lc = A.L;
-  {
-    const TL<V> Ls = shared_level<D, V>(A, ls, sm);
-    for (int t = tid; t < A.lv[ls].nv * D; t += NT) Ls.b[t] = __ldcg(A.lv[ls].b + t);
-  }
-  __syncthreads();
-  for (int l = ls; l < Lc; ++l) {
+  for (int l = lfrom; l < lto; ++l) {
     const TL<V> L = shared_level<D, V>(A, l, sm);
     tail_sweep<D, G, V, S, 0, true>(L, g, ng, lane, CtaSync());
     for (int base = 0; base < L.nv; base += ng) row_pass<D, G, V, S, 2, TL<V>, true>(L, base + g, base + g < L.nv, lane);
@@ -748,20 +749,106 @@ __device__ void tail_one_cta(const TailArgs<V>& A) {
     for (int I = tid; I < L.nvc; I += NT) restrict_row<D, V, TL<V>, true>(L, I);
     __syncthreads();
   }
-  {
-    const TL<V> Lcs = shared_level<D, V>(A, Lc, sm);
-    if (threadIdx.x < 32) coarse_solve_warp<V, true>(A.co, Lcs.b, Lcs.x);
-  }
-  __syncthreads();
-  for (int l = Lc - 1; l >= ls; --l) {
+}
+
+// Levels lfrom-1 down to lto of the one-CTA part, going up: prolongation and
+// correction from level l+1's x, then the backward sweep.
+template <int D, typename V, typename S>
+__device__ __forceinline__ void one_cta_up(const TailArgs<V>& A, V* sm, int lfrom, int lto) {
+  constexpr int G = tail_g<D>();
+  const int ng = blockDim.x / G, g = (int)threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int l = lfrom - 1; l >= lto; --l) {
     const TL<V> L = shared_level<D, V>(A, l, sm);
     for (int i = tid; i < L.nv; i += NT) prolong_row<D, V, TL<V>, true>(L, i);
     __syncthreads();
     tail_sweep<D, G, V, S, 1, true>(L, g, ng, lane, CtaSync());
   }
+}
+
+// Levels ls..L of the V-cycle on one CTA: phases separated by CTA barriers,
+// only b_ls comes in and x_ls goes out.
+template <int D, typename V, typename S>
+__device__ void tail_one_cta(const TailArgs<V>& A) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  V* sm = reinterpret_cast<V*>(tail_smem);
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int ls = A.ls, Lc = A.L;
+  {
+    const TL<V> Ls = shared_level<D, V>(A, ls, sm);
+    for (int t = tid; t < A.lv[ls].nv * D; t += NT) Ls.b[t] = __ldcg(A.lv[ls].b + t);
+  }
+  __syncthreads();
+  one_cta_down<D, V, S>(A, sm, ls, Lc);
+  {
+    const TL<V> Lcs = shared_level<D, V>(A, Lc, sm);
+    if (threadIdx.x < 32) coarse_solve_warp<V, true>(A.co, Lcs.b, Lcs.x);
+  }
+  __syncthreads();
+  one_cta_up<D, V, S>(A, sm, Lc, ls);
   {
     const TL<V> Ls = shared_level<D, V>(A, ls, sm);
     for (int t = tid; t < A.lv[ls].nv * D; t += NT) __stcg(A.lv[ls].x + t, Ls.x[t]);
+  }
+}
+
+// x_kd = M b_kd on every CTA of the cluster (FP32): each CTA stages b_kd
+// (global, written before the cluster barrier) in shared memory, zero-padded
+// to the row stride; then one warp per row of M, lanes over 16-byte column
+// groups, four partial sums, a shuffle sum, the row's x to global.
+__device__ __forceinline__ void dense_level_rows(const TailArgs<float>& A, float* sb, int rank, int nct) {
+  const int n = A.dn, ld = A.dld;
+  const float* b = A.lv[A.kd].b;
+  float* x = A.lv[A.kd].x;
+  for (int t = threadIdx.x; t < ld; t += blockDim.x) sb[t] = t < n ? __ldcg(b + t) : 0.0f;
+  __syncthreads();
+  const float4* sb4 = reinterpret_cast<const float4*>(sb);
+  const int wpc = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const int nw = nct * wpc, ld4 = ld >> 2;
+  for (int t = rank * wpc + ((int)threadIdx.x >> 5); t < n; t += nw) {
+    const float4* m4 = reinterpret_cast<const float4*>(A.dm + (long long)t * ld);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll 4
+    for (int j = lane; j < ld4; j += 32) {
+      const float4 mv = __ldg(m4 + j), bv = sb4[j];
+      a0 += mv.x * bv.x;
+      a1 += mv.y * bv.y;
+      a2 += mv.z * bv.z;
+      a3 += mv.w * bv.w;
+    }
+    float acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) __stcg(x + t, acc);
+  }
+}
+
+// The one-CTA part with a dense level kd: levels ls..kd-1 on CTA 0, then
+// x_kd = M b_kd on the whole cluster, then back up on CTA 0.  b_kd and x_kd
+// pass between the CTAs through global memory across cluster barriers.
+template <int D, typename V, typename S>
+__device__ void tail_dense_part(const TailArgs<V>& A, int rank, int nct) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  V* sm = reinterpret_cast<V*>(tail_smem);
+  const int ls = A.ls, kd = A.kd, n_ls = A.lv[ls].nv * D, n_kd = A.dn;
+  if (rank == 0 && kd > ls) {
+    const TL<V> Ls = shared_level<D, V>(A, ls, sm);
+    for (int t = threadIdx.x; t < n_ls; t += blockDim.x) Ls.b[t] = __ldcg(A.lv[ls].b + t);
+    __syncthreads();
+    one_cta_down<D, V, S>(A, sm, ls, kd);
+    const TL<V> Lk = shared_level<D, V>(A, kd, sm);
+    for (int t = threadIdx.x; t < n_kd; t += blockDim.x) __stcg(A.lv[kd].b + t, Lk.b[t]);
+  }
+  cluster_sync_all();
+  dense_level_rows(A, sm + A.dsoff, rank, nct);
+  cluster_sync_all();
+  if (rank == 0 && kd > ls) {
+    const TL<V> Lk = shared_level<D, V>(A, kd, sm);
+    for (int t = threadIdx.x; t < n_kd; t += blockDim.x) Lk.x[t] = __ldcg(A.lv[kd].x + t);
+    __syncthreads();
+    one_cta_up<D, V, S>(A, sm, kd, ls);
+    const TL<V> Ls = shared_level<D, V>(A, ls, sm);
+    for (int t = threadIdx.x; t < n_ls; t += blockDim.x) __stcg(A.lv[ls].x + t, Ls.x[t]);
   }
 }
 
@@ -786,7 +873,14 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constan
     for (int I = tid; I < L.nvc; I += NT) restrict_row<D, V>(L, I);
     cluster_sync_all();
   }
-  if (rank == 0) tail_one_cta<D, V, S>(A);
+  if constexpr (std::is_same<V, float>::value) {
+    if (A.kd >= 0)
+      tail_dense_part<D, V, S>(A, rank, nct);
+    else if (rank == 0)
+      tail_one_cta<D, V, S>(A);
+  } else {
+    if (rank == 0) tail_one_cta<D, V, S>(A);
+  }
   cluster_sync_all();
   for (int l = ls - 1; l >= l0; --l) {
     const TL<V>& L = A.lv[l];
@@ -794,6 +888,30 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constan
     cluster_sync_all();
     tail_sweep<D, G, V, S, 1, false>(L, gg, NG, lane, ClusterSync());
   }
+}
+
+// The dense level's matrix, column by column: CTA j runs the one-CTA V-cycle
+// from level kd (= A.ls) on the unit vector e_j, with its own coarse-solve
+// scratch, and writes the result to column j of M (row-major, n x n).
+template <int D, typename V, typename S>
+__global__ void __launch_bounds__(TAIL_THREADS) dense_level_kernel(const __grid_constant__ TailArgs<V> A, V* M,
+                                                                   double* yscratch) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  V* sm = reinterpret_cast<V*>(tail_smem);
+  const int kd = A.ls, Lc = A.L, n = A.dn, ld = A.dld, j = blockIdx.x;
+  const TL<V> Lk = shared_level<D, V>(A, kd, sm);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) Lk.b[t] = t == j ? V(1) : V(0);
+  __syncthreads();
+  one_cta_down<D, V, S>(A, sm, kd, Lc);
+  {
+    CoarseArgs co = A.co;
+    co.y = yscratch + (long long)j * co.n;
+    const TL<V> Lcs = shared_level<D, V>(A, Lc, sm);
+    if (threadIdx.x < 32) coarse_solve_warp<V, true>(co, Lcs.b, Lcs.x);
+  }
+  __syncthreads();
+  one_cta_up<D, V, S>(A, sm, Lc, kd);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) M[(long long)t * ld + j] = Lk.x[t];
 }
 
 // ------------------------------------------------------------------ outer CG (FP64)
@@ -1161,6 +1279,8 @@ struct EngineBase {
   virtual double time(Ctx& c, int which, int level, int reps, double* bytes) = 0;
   // refill the engine's own copies of operator values (same structure)
   virtual void refresh_values() = 0;
+  // the dense level and the order of its matrix, (-1, 0) if none
+  virtual void dense_level(int* k, int* n) const = 0;
 };
 
 // Lanes per row: few enough that a CTA pass covers many rows (the sweeps are
@@ -1178,6 +1298,10 @@ struct Engine : EngineBase {
   int L = 0;       // number of levels
   int lt = 0;      // first tail level
   int nct = 1;     // CTAs in the tail cluster
+  int kd = -1;     // dense level (FP32 vectors): x_kd = M b_kd replaces the cycle below it
+  int dn = 0;      // order of M
+  int dld = 0;     // row stride of M (dn rounded up to a multiple of 4)
+  DevBuf<V> dm;    // M, row-major, zero-padded columns
   int sms_ = 1;    // SMs of the device
   std::vector<LV<V>> lv;
   std::vector<int> G;
@@ -1345,6 +1469,7 @@ struct Engine : EngineBase {
           lv[l].nhi);
       check_launch("split_parts");
     }
+    build_dense_level();
     VASMG_CUDA(cudaStreamSynchronize(s));
   }
 
@@ -1482,6 +1607,9 @@ struct Engine : EngineBase {
       c->cta_capacity = c->cta_capacity ? std::min<int>(c->cta_capacity, (int)cap) : (int)cap;
     }
     VASMG_CUDA(cudaFuncSetAttribute(tail_kernel<D, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM_MAX));
+    if constexpr (std::is_same<V, float>::value)
+      VASMG_CUDA(cudaFuncSetAttribute(dense_level_kernel<D, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TAIL_SMEM_MAX));
     // tail cluster size: as many CTAs (<= 16) as the work of the tail levels warrants
     {
       i64 work = 0;
@@ -1519,6 +1647,7 @@ struct Engine : EngineBase {
     co.y = coarse_y.get();
     co.n = (int)c->nc;
     co.d = D;
+    build_dense_level();
     // CG state
     SolveLevel& s0 = c->S[0];
     const i64 n = s0.nv * D;
@@ -1622,13 +1751,20 @@ struct Engine : EngineBase {
       }
     }
   }
-  void tail(int l0, cudaStream_t s) {
-    TailArgs<V> ta;
+  // First level of the one-CTA part of a tail that starts at level l0.
+  int one_cta_start(int l0) const {
+    int ls = L - 1;
+    while (ls > l0 && c->S[ls - 1].nv <= ONE_CTA_NV) --ls;
+    return ls;
+  }
+  // The tail's level tables; levels ls..L-1 get shared-memory slots.
+  // Returns the dynamic shared memory in bytes.
+  size_t fill_tail_args(TailArgs<V>& ta, int l0, int ls) {
     std::memset(&ta, 0, sizeof(ta));
     ta.l0 = l0;
     ta.L = L - 1;
-    ta.ls = L - 1;
-    while (ta.ls > l0 && c->S[ta.ls - 1].nv <= ONE_CTA_NV) --ta.ls;
+    ta.ls = ls;
+    ta.kd = -1;
     size_t smem = 0;
     for (int l = ta.ls; l < L; ++l) {
       ta.soff[l] = (int)(smem / sizeof(V));
@@ -1663,6 +1799,56 @@ struct Engine : EngineBase {
       t.xc = v.xc;
     }
     ta.co = co;
+    return smem;
+  }
+  // The V-cycle from the dense level kd down, as the matrix M (one CTA per
+  // column, the same arithmetic as the tail's one-CTA part).  Rebuilt when
+  // the operators' values change.
+  void dense_level(int* k, int* n) const override {
+    *k = kd;
+    *n = dn;
+  }
+  void build_dense_level() {
+    kd = -1;
+    dn = 0;
+    if (!c->dense_coarse) return;
+    if constexpr (std::is_same<V, float>::value) {
+      const int ls = one_cta_start(lt);
+      for (int l = ls; l < L; ++l) {
+        const i64 n = c->S[l].nv * D;
+        if (n * n <= (i64)nct * DENSE_ROWS_PER_CTA * DENSE_ROWS_PER_CTA) {
+          kd = l;
+          break;
+        }
+      }
+      if (kd < 0) return;
+      cudaStream_t s = c->stream;
+      dn = (int)(c->S[kd].nv * D);
+      dld = (dn + 3) / 4 * 4;
+      if (dm.n != (i64)dn * dld) dm.alloc((i64)dn * dld, s);
+      dm.zero();
+      DevBuf<double> ys;
+      ys.alloc((i64)dn * co.n, s);
+      TailArgs<V> ta;
+      const size_t smem = fill_tail_args(ta, kd, kd);
+      ta.dn = dn;
+      ta.dld = dld;
+      dense_level_kernel<D, V, S><<<dn, TAIL_THREADS, smem, s>>>(ta, dm.get(), ys.get());
+      check_launch("dense_level");
+    }
+  }
+  void tail(int l0, cudaStream_t s) {
+    TailArgs<V> ta;
+    size_t smem = fill_tail_args(ta, l0, one_cta_start(l0));
+    if (kd >= 0 && kd >= ta.ls) {
+      ta.kd = kd;
+      ta.dn = dn;
+      ta.dld = dld;
+      ta.dm = dm.get();
+      ta.dsoff = (int)(smem / sizeof(V));  // fill_tail_args keeps smem a multiple of 16 bytes
+      smem += sizeof(V) * (size_t)dld;
+      VASMG_CHECK(smem <= (size_t)TAIL_SMEM_MAX, VASMG_ERR_UNSUPPORTED, "tail levels too large for shared memory");
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nct);
     cfg.blockDim = dim3(TAIL_THREADS);
@@ -1981,6 +2167,12 @@ struct Engine : EngineBase {
            (double)c->S[l + 1].nv * D * sizeof(V) + 2.0 * (double)c->S[l].nv * D * sizeof(V);
   }
   double tail_bytes(int l0) {
+    if (kd >= 0 && kd >= one_cta_start(l0)) {
+      // levels l0..kd-1, then M (with its padding) and b_kd, x_kd
+      double b = (double)dn * dld * sizeof(V) + 2.0 * dn * sizeof(V);
+      for (int l = l0; l < kd; ++l) b += down_bytes(l) + up_bytes(l);
+      return b;
+    }
     double b = (double)c->nc * c->nc * 8.0;
     for (int l = l0; l + 1 < L; ++l) b += down_bytes(l) + up_bytes(l);
     return b;
@@ -2075,6 +2267,12 @@ void apply_op(Ctx& c, int op, int level, const double* x_dev, double* y_dev) { c
 
 double time_kernel(Ctx& c, int which, int level, int reps, double* bytes) {
   return c.eng->time(c, which, level, reps, bytes);
+}
+
+void dense_level_info(Ctx& c, int* kd, int* dn) {
+  *kd = -1;
+  *dn = 0;
+  if (c.eng) c.eng->dense_level(kd, dn);
 }
 
 }  // namespace vasmg

@@ -41,6 +41,7 @@ TRAFFIC = {
     ("square1024_checker", "bwd_sweep_l1"): 235154432.0,
     ("square1024_checker", "fwd_sweep_l1"): 124179200.0,
     ("square1024_checker", "residual_l0"): 75392256.0,
+    ("square1024_checker", "tail_l4"): 29569280.0,
     ("square1024_checker", "spmv64_sell"): 314983424.0,
 }
 TOL = 1e-6

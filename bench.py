@@ -411,6 +411,8 @@ def ours(args):
                        "precision": args.precision, "tol": TOL, "levels": len(levels),
                        "level_vertices": [lv[0] for lv in levels], "level_blocks": [lv[1] for lv in levels],
                        "level_colours": [lv[2] for lv in levels], "op_complexity": st.op_complexity,
+                       "lanes_per_row": [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)],
+                       "dense_level": [int(v) for v in s.export(vasmg.EXPORT_DENSE, 0, np.int64)],
                        "setup_ms": st.setup_ms, "l2": "operators > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "limiter": "latency" if top.startswith("tail") else "latency/HBM",

@@ -101,6 +101,15 @@ typedef struct {
                                   one matrix-vector product: the same linear
                                   operator up to FP32 rounding.  0: run the
                                   recursion.  Ignored by VASMG_FP64. */
+  int32_t autotune;            /* 1 (default): at setup, time each region
+                                  level's sweeps with 4, 8, 16 and 32 lanes per
+                                  row and keep the fastest.  The lane count
+                                  changes the order of additions within a row,
+                                  so the choice is cached per level signature
+                                  (dim, precision, vertices, blocks) for the
+                                  process: handles of the same problem give the
+                                  same bits.  0: lanes per row by rule from the
+                                  mean row length. */
   void* stream;                /* cudaStream_t used for all device work */
 } vasmg_options;
 
@@ -248,7 +257,9 @@ enum {
   VASMG_EXPORT_BOX = 14,         /* f64[2] bounding square (m, M) */
   VASMG_EXPORT_LIFT = 15,        /* f64[n] A u_D of the Dirichlet data */
   VASMG_EXPORT_VOL = 16,         /* f64[n_elements] element measures */
-  VASMG_EXPORT_DENSE = 17        /* i64[2] (k, n_k) of the dense level, (-1, 0) if none (level ignored) */
+  VASMG_EXPORT_DENSE = 17,       /* i64[2] (k, n_k) of the dense level, (-1, 0) if none (level ignored) */
+  VASMG_EXPORT_LANES = 18        /* i32[n_levels] lanes per row of each level's region sweeps, 0 for the
+                                    levels the tail launch runs (level ignored) */
 };
 
 /* Copy an exported array to host buffer buf (NULL: only report the size).

@@ -101,6 +101,7 @@ int vasmg_default_options(int dim, vasmg_options* out) {
   out->max_iters = 1000;
   out->use_graph = 1;
   out->dense_coarse = 1;
+  out->autotune = 1;
   out->stream = nullptr;
   return VASMG_OK;
 }
@@ -119,7 +120,7 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   if (o.n_pre != 1 || o.n_post != 1) return VASMG_ERR_UNSUPPORTED;
   if (o.precision < VASMG_FP64 || o.precision > VASMG_FP32_VCYCLE_BF16_SMOOTH) return VASMG_ERR_INVALID_ARG;
   if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096 || o.max_iters <= 0 || o.max_ctas < 0 ||
-      o.dense_coarse < 0 || o.dense_coarse > 1)
+      o.dense_coarse < 0 || o.dense_coarse > 1 || o.autotune < 0 || o.autotune > 1)
     return VASMG_ERR_INVALID_ARG;
   vasmg_ctx* h = new vasmg_ctx();
   struct Guard {
@@ -140,6 +141,7 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   c.use_graph = o.use_graph;
   c.max_ctas = o.max_ctas > 0 ? o.max_ctas : 0;
   c.dense_coarse = o.dense_coarse;
+  c.autotune = o.autotune;
   c.coarse_max_dofs = o.coarse_max_dofs;
   c.user_stream = (cudaStream_t)o.stream;
   VASMG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
@@ -379,6 +381,12 @@ int vasmg_export(vasmg_handle h, int32_t what, int32_t level, void* buf, int64_t
     }
     case VASMG_EXPORT_LIFT: dev(c.lift.get(), (size_t)c.n * 8); break;
     case VASMG_EXPORT_VOL: dev(c.vol.get(), (size_t)c.ne * 8); break;
+    case VASMG_EXPORT_LANES: {
+      std::vector<int32_t> g(c.C.size(), 0);
+      lanes_info(c, g.data(), (int)g.size());
+      put(g.data(), g.size() * sizeof(int32_t));
+      break;
+    }
     case VASMG_EXPORT_DENSE: {
       int kd = -1, dn = 0;
       dense_level_info(c, &kd, &dn);

@@ -182,6 +182,7 @@ struct Ctx {
   int dim = 2, K = 31, T = 4, precision = VASMG_FP64, max_iters = 1000, use_graph = 1;
   int max_ctas = 0;       // cap on the CTAs of one sweep launch (0: device capacity)
   int dense_coarse = 1;   // FP32-vector modes: apply the cycle below the dense level as one matrix
+  int autotune = 1;       // measure the lanes per row of each region level at setup
   int ctas_used = 0;      // largest sweep grid this handle launches
   int cta_capacity = 0;   // CTAs of the sweep kernels the device holds at once
   i64 coarse_max_dofs = 0;
@@ -244,6 +245,7 @@ int solve_dev(Ctx& c, const double* F_dev, double* U_dev, double tol, vasmg_stat
 void apply_op(Ctx& c, int op, int level, const double* x_dev, double* y_dev);
 double time_kernel(Ctx& c, int which, int level, int reps, double* bytes);
 void dense_level_info(Ctx& c, int* kd, int* dn);  // the engine's dense level, (-1, 0) if none
+void lanes_info(Ctx& c, int32_t* g, int n);       // lanes per row of the region levels, 0 elsewhere
 void destroy_solver_state(Ctx& c);
 
 // small device helpers shared across files

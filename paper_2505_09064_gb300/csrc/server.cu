@@ -93,6 +93,8 @@ struct vasmg_server {
     opt.precision = o.precision;
     opt.max_iters = o.max_iters;
     opt.max_ctas = max_ctas;
+    // lanes per row by rule: a request's latency carries no tuning runs
+    opt.autotune = 0;
     opt.stream = stream;
     vasmg_request_stats& st = r->st;
     st.n_rhs = (int32_t)r->F.size();

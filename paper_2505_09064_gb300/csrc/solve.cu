@@ -40,6 +40,9 @@
 // round trip per iteration).
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "common.cuh"
@@ -1281,7 +1284,29 @@ struct EngineBase {
   virtual void refresh_values() = 0;
   // the dense level and the order of its matrix, (-1, 0) if none
   virtual void dense_level(int* k, int* n) const = 0;
+  // lanes per row of the region levels (levels below the tail), 0 elsewhere
+  virtual void lanes(int32_t* g, int n) const = 0;
 };
+
+// Lanes per row measured rather than picked by rule (vasmg_options.autotune):
+// G changes the order of additions within a row, so a level's choice is kept
+// per level signature for the whole process, and every handle of the same
+// problem sweeps with the same G and gives the same bits.
+struct LaneKey {
+  int d, precision;
+  long long nv, nnz;
+  bool operator<(const LaneKey& o) const {
+    return std::tie(d, precision, nv, nnz) < std::tie(o.d, o.precision, o.nv, o.nnz);
+  }
+};
+static std::mutex& lane_cache_mutex() {
+  static std::mutex m;
+  return m;
+}
+static std::map<LaneKey, int>& lane_cache() {
+  static std::map<LaneKey, int> m;
+  return m;
+}
 
 // Lanes per row: few enough that a CTA pass covers many rows (the sweeps are
 // bound by the latency of their dependent loads, not by lane utilisation).
@@ -1679,6 +1704,7 @@ struct Engine : EngineBase {
     cga.sc = sc.get();
     cga.cond = 0;
     build_sell();
+    if (c->autotune) autotune_lanes();
     VASMG_CUDA(cudaStreamSynchronize(s));
   }
 
@@ -1686,6 +1712,72 @@ struct Engine : EngineBase {
   void occ(int* bd, int* bu) {
     VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bd, vdown_kernel<D, GG, V, S>, DF_THREADS, 0));
     VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bu, vup_kernel<D, GG, V, S>, DF_THREADS, 0));
+  }
+  // CTAs of the sweep kernels with g lanes per row that the device holds at once
+  i64 sweep_capacity(int g) {
+    int bd = 1, bu = 1;
+    switch (g) {
+      case 4: occ<4>(&bd, &bu); break;
+      case 8: occ<8>(&bd, &bu); break;
+      case 16: occ<16>(&bd, &bu); break;
+      default: occ<32>(&bd, &bu); break;
+    }
+    return (i64)std::min(bd, bu) * sms_;
+  }
+
+  // For every region level, time the forward sweep, the residual and the
+  // backward sweep with each G of {4, 8, 16, 32} whose kernels can hold the
+  // level's region grid (CUDA events, one warm-up and three timed runs) and
+  // keep the fastest.  A level signature measured before in this process
+  // (by this or another handle) reuses that choice.
+  void autotune_lanes() {
+    cudaStream_t s = c->stream;
+    for (int l = 0; l < lt; ++l) {
+      const SolveLevel& sl = c->S[l];
+      const LaneKey key{D, c->precision, (long long)sl.nv, (long long)sl.nnz};
+      {
+        std::lock_guard<std::mutex> lock(lane_cache_mutex());
+        auto it = lane_cache().find(key);
+        if (it != lane_cache().end()) {
+          if (sweep_capacity(it->second) >= lv[l].R) G[l] = it->second;
+          continue;
+        }
+      }
+      VASMG_CUDA(cudaMemsetAsync(lv[l].x, 0, sizeof(V) * (size_t)sl.nv * D, s));
+      VASMG_CUDA(cudaMemsetAsync(lv[l].b, 0, sizeof(V) * (size_t)sl.nv * D, s));
+      clear_abort(s);
+      cudaEvent_t e0, e1;
+      VASMG_CUDA(cudaEventCreate(&e0));
+      VASMG_CUDA(cudaEventCreate(&e1));
+      int best_g = G[l];
+      float best_ms = 0.0f;
+      for (int g : {4, 8, 16, 32}) {
+        if (sweep_capacity(g) < lv[l].R) continue;
+        G[l] = g;
+        auto run = [&]() {
+          down(l, 1, s);
+          down(l, 2, s);
+          up(l, 2, s);
+        };
+        run();
+        VASMG_CUDA(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 3; ++rep) run();
+        VASMG_CUDA(cudaEventRecord(e1, s));
+        VASMG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        VASMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (best_ms == 0.0f || ms < best_ms) {
+          best_ms = ms;
+          best_g = g;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      VASMG_CHECK(read_abort(s) == 0, VASMG_ERR_TIMEOUT, "a device wait gave up");
+      std::lock_guard<std::mutex> lock(lane_cache_mutex());
+      const int chosen = lane_cache().emplace(key, best_g).first->second;  // another handle may have been first
+      G[l] = sweep_capacity(chosen) >= lv[l].R ? chosen : best_g;
+    }
   }
 
   // ---------------------------------------------------------------- launches
@@ -1807,6 +1899,9 @@ struct Engine : EngineBase {
   void dense_level(int* k, int* n) const override {
     *k = kd;
     *n = dn;
+  }
+  void lanes(int32_t* g, int n) const override {
+    for (int l = 0; l < n; ++l) g[l] = l < lt && l < (int)G.size() ? G[l] : 0;
   }
   void build_dense_level() {
     kd = -1;
@@ -2267,6 +2362,11 @@ void apply_op(Ctx& c, int op, int level, const double* x_dev, double* y_dev) { c
 
 double time_kernel(Ctx& c, int which, int level, int reps, double* bytes) {
   return c.eng->time(c, which, level, reps, bytes);
+}
+
+void lanes_info(Ctx& c, int32_t* g, int n) {
+  for (int l = 0; l < n; ++l) g[l] = 0;
+  if (c.eng) c.eng->lanes(g, n);
 }
 
 void dense_level_info(Ctx& c, int* kd, int* dn) {

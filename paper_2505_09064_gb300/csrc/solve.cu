@@ -1275,6 +1275,33 @@ __global__ void from_solve_kernel(const V* __restrict__ in, double* __restrict__
 
 // ------------------------------------------------------------------ engine
 
+// Lengths of each row's lower (earlier-colour) and upper parts; entry nv is
+// 0 so that exclusive scans of the n + 1 entries end with the totals.
+__global__ void part_lengths_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ sp, int nv,
+                                    int32_t* __restrict__ nlo, int32_t* __restrict__ nhi) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nv; i += gridDim.x * blockDim.x) {
+    nlo[i] = i < nv ? sp[i] - rp[i] : 0;
+    nhi[i] = i < nv ? rp[i + 1] - sp[i] : 0;
+  }
+}
+
+// Region adjacency bits: for every block (i, j) of a row i in region k whose
+// column j lies in region k2 != k, bit k2 of region k's W words.  A word
+// already holding the bit is not written again.
+__global__ void region_bits_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int nv,
+                                   const int32_t* __restrict__ reg, int W, unsigned long long* bits) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+    const int k = reg[i];
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int k2 = reg[ci[e]];
+      if (k2 == k) continue;
+      unsigned long long* w = bits + (long long)k * W + (k2 >> 6);
+      const unsigned long long m = 1ull << (k2 & 63);
+      if (!(*(volatile unsigned long long*)w & m)) atomicOr(w, m);
+    }
+  }
+}
+
 struct EngineBase {
   virtual ~EngineBase() {}
   virtual int solve(Ctx& c, const double* F, double* U, double tol, vasmg_stats* st) = 0;
@@ -1415,22 +1442,19 @@ struct Engine : EngineBase {
       list_d.upload(list.data(), (i64)list.size());
     };
     {
-      std::vector<int32_t> rp = sl.rp.download(), ci = sl.ci.download(), spv = sl.sp.download();
-      i64 lo = 0;
-      for (int i = 0; i < nv; ++i) lo += spv[i] - rp[i];
+      // the blocks split by part (lower / upper), each part contiguous: row
+      // pointers by exclusive scans of the part lengths, on the device
+      rpl_dev[l].alloc(nv + 1, s);
+      rph_dev[l].alloc(nv + 1, s);
+      part_lengths_kernel<<<grid_for(nv + 1, 256), 256, 0, s>>>(sl.rp.get(), sl.sp.get(), nv, rpl_dev[l].get(),
+                                                                 rph_dev[l].get());
+      check_launch("part_lengths");
+      scan_exclusive_i32(rpl_dev[l].get(), rpl_dev[l].get(), nv + 1, s);
+      scan_exclusive_i32(rph_dev[l].get(), rph_dev[l].get(), nv + 1, s);
+      const i64 lo = fetch(rpl_dev[l].get() + nv, s);
       nnz_lo[l] = lo;
-      // the blocks split by part (lower / upper), each part contiguous
       {
         const i64 hi = sl.nnz - lo;
-        std::vector<int> rpl(nv + 1, 0), rph(nv + 1, 0);
-        for (int i = 0; i < nv; ++i) {
-          rpl[i + 1] = rpl[i] + (spv[i] - rp[i]);
-          rph[i + 1] = rph[i] + (rp[i + 1] - spv[i]);
-        }
-        rpl_dev[l].alloc(nv + 1, s);
-        rpl_dev[l].upload(rpl.data(), nv + 1);
-        rph_dev[l].alloc(nv + 1, s);
-        rph_dev[l].upload(rph.data(), nv + 1);
         cil_dev[l].alloc(std::max<i64>(lo, 1), s);
         cih_dev[l].alloc(std::max<i64>(hi, 1), s);
         offl_dev[l].alloc(std::max<i64>((i64)D * D * lo, 1), s);
@@ -1451,13 +1475,20 @@ struct Engine : EngineBase {
         v.offh = offh_dev[l].get();
         v.nhi = hi;
       }
-      std::vector<u64> bits((size_t)R * W, 0);
-      for (int i = 0; i < nv; ++i)
-        for (int e = rp[i]; e < rp[i + 1]; ++e) {
-          const int k2 = reg[ci[e]];
-          if (k2 != reg[i]) bits[(size_t)reg[i] * W + k2 / 64] |= 1ull << (k2 % 64);
-        }
-      to_csr(bits, nb_rp[l], nb[l]);
+      // region adjacency: bit k2 of region k's words for every block (i, j)
+      // with i in region k and j in region k2 != k, set on the device
+      DevBuf<int32_t> reg_d;
+      reg_d.alloc(std::max(nv, 1), s);
+      reg_d.upload(reg.data(), nv);
+      DevBuf<u64> bits_d;
+      bits_d.alloc((i64)R * W, s);
+      bits_d.zero();
+      if (nv > 0) {
+        region_bits_kernel<<<grid_for(nv, 256), 256, 0, s>>>(sl.rp.get(), sl.ci.get(), nv, reg_d.get(), W,
+                                                             (unsigned long long*)bits_d.get());
+        check_launch("region_bits");
+      }
+      to_csr(bits_d.download(), nb_rp[l], nb[l]);
     }
     rs_dev[l].alloc((i64)RS.size(), s);
     rs_dev[l].upload(RS.data(), (i64)RS.size());

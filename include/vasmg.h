@@ -350,6 +350,15 @@ const char* vasmg_error_string(int code);
 /* Human-readable detail of the last error raised on the calling thread. */
 const char* vasmg_last_error_detail(void);
 
+/* Failure detection without a fault: runs the bounded wait of the sweep
+ * kernels (the neighbour-region stage wait) in one CTA on its own stream,
+ * against a stage word that nothing publishes.  The wait gives up after its
+ * iteration limit (about 0.1-1 s), raises the abort flag and returns, so the
+ * call returns VASMG_ERR_TIMEOUT and the context stays usable; *elapsed_ms
+ * (may be NULL) receives the kernel's duration.  VASMG_OK would mean the wait
+ * was satisfied, which cannot happen. */
+int vasmg_probe_wait_timeout(double* elapsed_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -519,4 +519,10 @@ const char* vasmg_error_string(int code) {
 // Detail of the last error on this thread (not part of the stable ABI).
 const char* vasmg_last_error_detail(void) { return g_last_error.c_str(); }
 
+int vasmg_probe_wait_timeout(double* elapsed_ms) {
+  VASMG_API_BEGIN
+  return probe_wait_timeout(elapsed_ms);
+  VASMG_API_END
+}
+
 }  // extern "C"

@@ -246,6 +246,7 @@ void apply_op(Ctx& c, int op, int level, const double* x_dev, double* y_dev);
 double time_kernel(Ctx& c, int which, int level, int reps, double* bytes);
 void dense_level_info(Ctx& c, int* kd, int* dn);  // the engine's dense level, (-1, 0) if none
 void lanes_info(Ctx& c, int32_t* g, int n);       // lanes per row of the region levels, 0 elsewhere
+int probe_wait_timeout(double* elapsed_ms);       // the bounded device wait run out on purpose
 void destroy_solver_state(Ctx& c);
 
 // small device helpers shared across files

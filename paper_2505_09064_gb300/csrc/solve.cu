@@ -434,6 +434,15 @@ __device__ __forceinline__ bool wait_regions(const int* __restrict__ list, int n
   return s_ok != 0;
 }
 
+// The bounded wait on its own: one CTA waits for a stage word that nothing
+// publishes.  The wait must give up after SPIN_LIMIT polls, raise the abort
+// flag and return; *result is 1 if the wait was satisfied, 2 if it gave up.
+__global__ void wait_probe_kernel(const int* __restrict__ list, const unsigned long long* word, int* abort_flag,
+                                  int* result) {
+  const bool ok = wait_regions(list, 1, word, 1u, 1u, abort_flag);
+  if (threadIdx.x == 0) *result = ok ? 1 : 2;
+}
+
 // Publish this region's stage once every thread of the CTA has written: the
 // barrier orders the CTA's writes before thread 0's release, and a release
 // is cumulative, so a CTA that acquires the stage sees all of them.
@@ -2398,6 +2407,39 @@ double time_kernel(Ctx& c, int which, int level, int reps, double* bytes) {
 void lanes_info(Ctx& c, int32_t* g, int n) {
   for (int l = 0; l < n; ++l) g[l] = 0;
   if (c.eng) c.eng->lanes(g, n);
+}
+
+int probe_wait_timeout(double* elapsed_ms) {
+  cudaStream_t s = nullptr;
+  VASMG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } guard{s};
+  DevBuf<unsigned long long> word;
+  DevBuf<int32_t> list, flags;
+  word.alloc(1, s);
+  word.zero();
+  list.alloc(1, s);
+  list.zero();
+  flags.alloc(2, s);
+  flags.zero();
+  cudaEvent_t e0, e1;
+  VASMG_CUDA(cudaEventCreate(&e0));
+  VASMG_CUDA(cudaEventCreate(&e1));
+  VASMG_CUDA(cudaEventRecord(e0, s));
+  wait_probe_kernel<<<1, 32, 0, s>>>(list.get(), word.get(), flags.get(), flags.get() + 1);
+  check_launch("wait_probe");
+  VASMG_CUDA(cudaEventRecord(e1, s));
+  VASMG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.0f;
+  VASMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (elapsed_ms) *elapsed_ms = ms;
+  const std::vector<int32_t> f = flags.download();
+  if (f[1] == 2 && f[0] == 1) return VASMG_ERR_TIMEOUT;
+  return f[1] == 1 ? VASMG_OK : VASMG_ERR_CUDA;
 }
 
 void dense_level_info(Ctx& c, int* kd, int* dn) {

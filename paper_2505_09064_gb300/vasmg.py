@@ -33,7 +33,8 @@ EXPORTED = ["vasmg_default_options", "vasmg_setup", "vasmg_assemble_load", "vasm
             "vasmg_num_levels", "vasmg_level_info", "vasmg_export", "vasmg_apply", "vasmg_time_kernel",
             "vasmg_last_launch_count", "vasmg_destroy", "vasmg_error_string", "vasmg_last_error_detail",
             "vasmg_coarse_solve_noalloc", "vasmg_server_default_opts", "vasmg_server_create",
-            "vasmg_server_submit", "vasmg_server_poll", "vasmg_server_destroy", "vasmg_update_data"]
+            "vasmg_server_submit", "vasmg_server_poll", "vasmg_server_destroy", "vasmg_update_data",
+            "vasmg_probe_wait_timeout"]
 
 OK, NOT_CONVERGED, PENDING = 0, 1, 2
 
@@ -116,6 +117,8 @@ def load():
     lib.vasmg_error_string.restype = C.c_char_p
     lib.vasmg_last_error_detail.argtypes = []
     lib.vasmg_last_error_detail.restype = C.c_char_p
+    lib.vasmg_probe_wait_timeout.argtypes = [C.POINTER(C.c_double)]
+    lib.vasmg_probe_wait_timeout.restype = C.c_int
     _lib = lib
     return lib
 
@@ -202,6 +205,14 @@ def vasmg_solve_batch(handles, Fs, Us, tol: float = 1e-6):
     rc = _check(load().vasmg_solve_batch(k, H, Fp, Up, float(tol), st), "vasmg_solve_batch",
                 allow_not_converged=True)
     return rc, list(st)
+
+
+def vasmg_probe_wait_timeout():
+    """Run the sweeps' bounded wait against a word nothing publishes; returns
+    (return code, kernel milliseconds).  The code is VASMG_ERR_TIMEOUT."""
+    ms = C.c_double()
+    rc = load().vasmg_probe_wait_timeout(C.byref(ms))
+    return rc, ms.value
 
 
 def vasmg_num_levels(h) -> int:

@@ -30,11 +30,17 @@
 // acquire at GPU scope).  Every wait is bounded; a wait that gives up raises a
 // global abort flag and the solve returns VASMG_ERR_TIMEOUT.  The last CTA to
 // leave a launch advances its epoch.  Residual, restriction and prolongation
-// have no dependencies within themselves and run as plain kernels.
+// have no dependencies within themselves and run as plain kernels.  The
+// lanes per row G of each such level are timed at setup (autotune) or set by
+// rule from the mean row length.
 //
 // Levels with at most TAIL_NV vertices and the coarsest Cholesky solve run in
 // one thread-block-cluster kernel (hardware cluster barriers between phases;
 // the smallest levels on CTA 0 alone with their vectors in shared memory).
+// With FP32 vectors, the V-cycle from a small level k down is a fixed linear
+// map that setup precomputes as a dense matrix (the cycle applied to the unit
+// vectors); the tail then applies it as x_k = M b_k on the whole cluster
+// instead of recursing below k.
 //
 // The whole solve is one CUDA graph with a conditional WHILE node (no host
 // round trip per iteration).

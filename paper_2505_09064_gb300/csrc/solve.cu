@@ -112,6 +112,24 @@ __device__ __forceinline__ void stx(V* p, V v) {
   if constexpr (LC) *p = v;
   else __stcg(p, v);
 }
+// The D components of one vertex: one 8- or 16-byte load for D = 2 from
+// global memory (rows of 2 values are 8- / 16-byte aligned), else one load
+// per component.
+template <int D, bool LC = false, typename V>
+__device__ __forceinline__ void ldx_vertex(const V* p, V (&v)[D]) {
+  if constexpr (D == 2 && !LC && std::is_same<V, float>::value) {
+    const float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  } else if constexpr (D == 2 && !LC && std::is_same<V, double>::value) {
+    const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = ldx<LC>(p + a);
+  }
+}
 
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
@@ -257,8 +275,7 @@ __device__ __forceinline__ void row_pass(const L_t& L, int row, bool valid, int 
     V blk[D * D];
     const int j = seg_entry<D, V, S>(sg, e, ciA, offA, nA, ciB, offB, nB, blk);
     V xj[D];
-#pragma unroll
-    for (int bb = 0; bb < D; ++bb) xj[bb] = ldx<LC>(L.x + (long long)j * D + bb);
+    ldx_vertex<D, LC>((const V*)L.x + (long long)j * D, xj);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -330,8 +347,7 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
   for (int p = 0; p < NPF; ++p) {
     if (st.cj[p] >= 0) {
       V xj[D];
-#pragma unroll
-      for (int bb = 0; bb < D; ++bb) xj[bb] = ldx<LC>(L.x + (long long)st.cj[p] * D + bb);
+      ldx_vertex<D, LC>((const V*)L.x + (long long)st.cj[p] * D, xj);
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -349,8 +365,7 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
     V blk[D * D];
     const int j = seg_entry<D, V, S>(st.sg, e, ciA, offA, nA, ciB, offB, nB, blk);
     V xj[D];
-#pragma unroll
-    for (int bb = 0; bb < D; ++bb) xj[bb] = ldx<LC>(L.x + (long long)j * D + bb);
+    ldx_vertex<D, LC>((const V*)L.x + (long long)j * D, xj);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -379,8 +394,10 @@ __device__ __forceinline__ void restrict_row(const L_t& L, int I) {
   for (int t = __ldg(L.rrp + I); t < __ldg(L.rrp + I + 1); ++t) {
     const int i = __ldg(L.rci + t);
     const V w = __ldg((const V*)L.rw + t);
+    V ri[D];
+    ldx_vertex<D, LC>((const V*)L.r + (long long)i * D, ri);
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] += w * ldx<LC>((const V*)L.r + (long long)i * D + a);
+    for (int a = 0; a < D; ++a) acc[a] += w * ri[a];
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) stx<LC>((V*)L.bc + (long long)I * D + a, acc[a]);
@@ -394,8 +411,10 @@ __device__ __forceinline__ void prolong_row(const L_t& L, int i) {
   for (int t = __ldg(L.prp + i); t < __ldg(L.prp + i + 1); ++t) {
     const int J = __ldg(L.pci + t);
     const V w = __ldg((const V*)L.pw + t);
+    V xJ[D];
+    ldx_vertex<D, LC>((const V*)L.xc + (long long)J * D, xJ);
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] += w * ldx<LC>((const V*)L.xc + (long long)J * D + a);
+    for (int a = 0; a < D; ++a) acc[a] += w * xJ[a];
   }
   const uint8_t dm = __ldg(L.dead + i);
 #pragma unroll

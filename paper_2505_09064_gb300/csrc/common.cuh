@@ -161,7 +161,7 @@ struct SolveLevel {
   DevBuf<int32_t> ent;          // canonical block entry of each solve-order off-diagonal entry
   DevBuf<int32_t> perm, iperm;  // solve index -> canonical, canonical -> solve
   DevBuf<int32_t> rp, ci, sp;   // sp[i]: first entry of row i whose column is of a later colour
-  DevBuf<double> off64;         // [d*d][nnz]
+  DevBuf<double> off64;         // off-diagonal blocks, layout block_index()
   DevBuf<float> off32;
   DevBuf<__nv_bfloat16> off16;
   DevBuf<double> diag64;        // level 0: [d*d][nv]
@@ -309,6 +309,13 @@ __host__ __device__ inline u64 splitmix64(u64 x) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
+}
+
+// Storage of component q (row-major in the d x d block) of block k among n
+// blocks: 2 x 2 blocks are stored contiguously (one 8- or 16-byte load per
+// block), 3 x 3 blocks as d*d planes of n values (coalesced across rows).
+__host__ __device__ inline long long block_index(int q, long long k, long long n, int dd) {
+  return dd == 4 ? k * 4 + q : (long long)q * n + k;
 }
 
 inline int grid_for(i64 n, int threads, int cap = 1 << 20) {

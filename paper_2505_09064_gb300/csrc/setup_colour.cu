@@ -179,7 +179,7 @@ __global__ void planes_kernel(const double* __restrict__ cv, const int32_t* __re
                               S* __restrict__ out) {
   for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (i64)gridDim.x * blockDim.x) {
     const double* B = cv + (i64)ent[e] * dd;
-    for (int q = 0; q < dd; ++q) out[(i64)q * nnz + e] = cvt_from_double<S>(B[q]);
+    for (int q = 0; q < dd; ++q) out[block_index(q, e, nnz, dd)] = cvt_from_double<S>(B[q]);
   }
 }
 

@@ -98,6 +98,24 @@ template <>
 __device__ __forceinline__ float ldv<float, __nv_bfloat16>(const __nv_bfloat16* p) {
   return __bfloat162float(__ldg(p));
 }
+// A 2 x 2 block stored contiguously (4 values): one 16-byte load for FP32,
+// two for FP64, one 8-byte load for BF16.
+template <typename V, typename S>
+__device__ __forceinline__ void ldv4(const S* p, V (&a)[4]) {
+  if constexpr (std::is_same<S, float>::value) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    a[0] = t.x, a[1] = t.y, a[2] = t.z, a[3] = t.w;
+  } else if constexpr (std::is_same<S, double>::value) {
+    const double2 t0 = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    a[0] = t0.x, a[1] = t0.y, a[2] = t1.x, a[3] = t1.y;
+  } else {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&t.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&t.y);
+    a[0] = __low2float(lo), a[1] = __high2float(lo), a[2] = __low2float(hi), a[3] = __high2float(hi);
+  }
+}
 
 // vectors written inside a launch by other CTAs are read from L2 (.cg)
 // LC: the vector is produced and consumed by one CTA only, so plain (L1-cached)
@@ -150,17 +168,17 @@ struct LV {
   const int* rp;
   const int* ci;
   const int* sp;          // first entry of a later colour in each row
-  const void* off;        // planes [d*d][nnz] of S
+  const void* off;        // off-diagonal blocks of S, layout block_index()
   // the same blocks split by part, each part contiguous: lower = columns of
   // earlier colours, upper = later colours (the sweeps and the residual read
   // only the part they need)
   const int* rpl;
   const int* cil;
-  const void* offl;       // planes [d*d][nlo]
+  const void* offl;       // lower part, layout block_index() with n = nlo
   long long nlo;
   const int* rph;
   const int* cih;
-  const void* offh;       // planes [d*d][nhi]
+  const void* offh;       // upper part, layout block_index() with n = nhi
   long long nhi;
   const V* dinv;          // planes [d*d][nv]
   const uint8_t* dead;    // per vertex, bit a = component a removed
@@ -249,8 +267,13 @@ __device__ __forceinline__ int seg_entry(const RowSeg& r, int e, const int* ciA,
   (void)ciB;
   (void)offB;
   (void)nB;
+  if constexpr (D == 2) {
+    (void)n;
+    ldv4<V, S>(op + (long long)k * 4, a);  // 2D blocks are stored contiguously
+  } else {
 #pragma unroll
-  for (int q = 0; q < D * D; ++q) a[q] = ldv<V, S>(op + (long long)q * n + k);
+    for (int q = 0; q < D * D; ++q) a[q] = ldv<V, S>(op + (long long)q * n + k);
+  }
   return __ldg(cp + k);
 }
 
@@ -1212,12 +1235,12 @@ __global__ void split_parts_kernel(const int* __restrict__ rp, const int* __rest
     for (int k = k0; k < ks; ++k) {
       const long long d = rpl[i] + (k - k0);
       cil[d] = ci[k];
-      for (int q = 0; q < dd; ++q) offl[(long long)q * nlo + d] = off[(long long)q * nnz + k];
+      for (int q = 0; q < dd; ++q) offl[block_index(q, d, nlo, dd)] = off[block_index(q, k, nnz, dd)];
     }
     for (int k = ks; k < k1; ++k) {
       const long long d = rph[i] + (k - ks);
       cih[d] = ci[k];
-      for (int q = 0; q < dd; ++q) offh[(long long)q * nhi + d] = off[(long long)q * nnz + k];
+      for (int q = 0; q < dd; ++q) offh[block_index(q, d, nhi, dd)] = off[block_index(q, k, nnz, dd)];
     }
   }
 }
@@ -1275,7 +1298,7 @@ __global__ void sell_fill_kernel(const int* __restrict__ rows, const int* __rest
       } else if (rp[r] + k - 1 < rp[r + 1]) {
         const long long e = rp[r] + k - 1;
         col = ci[e];
-        for (int q = 0; q < DD; ++q) blk[q] = off[(long long)q * nnz + e];
+        for (int q = 0; q < DD; ++q) blk[q] = off[block_index(q, e, nnz, DD)];
       } else {
         col = r;
         for (int q = 0; q < DD; ++q) blk[q] = 0.0;

@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="lanes per row by rule (setup then launches no timing runs; for launch-indexed profiles)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of one CUDA graph per solve")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
@@ -295,7 +297,7 @@ def ours(args):
 
     def run_solver(precision, threshold=0):
         s = vasmg.Solver(prob, precision=precision, stream=stream, use_graph=not args.no_graph,
-                         threshold=threshold)
+                         threshold=threshold, autotune=not args.no_autotune)
         F = torch.zeros(n, dtype=torch.float64, device=dev)
         s.assemble_load(prob["body_force"], F)
         U = torch.zeros_like(F)

@@ -38,6 +38,10 @@ SAMPLE_N = 192          # CPU sample: same recipe at 192x192 vertices
 # DRAM bytes (read + write) of one launch from an ncu capture of the current
 # kernel (profiles/); absent when the kernel changed after the capture
 TRAFFIC = {
+    ("square1024_checker", "bwd_sweep_l1"): 235454464.0,
+    ("square1024_checker", "fwd_sweep_l1"): 124237312.0,
+    ("square1024_checker", "residual_l0"): 75727104.0,
+    ("square1024_checker", "tail_l4"): 29554688.0,
     ("square1024_checker", "spmv64_sell"): 314983424.0,
 }
 TOL = 1e-6

@@ -130,10 +130,11 @@ __device__ __forceinline__ void stx(V* p, V v) {
   if constexpr (LC) *p = v;
   else __stcg(p, v);
 }
-// The D components of one vertex: one 8- or 16-byte load for D = 2 from
-// global memory (rows of 2 values are 8- / 16-byte aligned), else one load
-// per component.
-template <int D, bool LC = false, typename V>
+// The D components of one vertex from global memory: one 8- or 16-byte load
+// for D = 2 (rows of 2 values are aligned to their size), a pair and a
+// single for D = 3 unless PAIR3 is false (the region sweeps: measured slower
+// there); one load per component from shared memory.
+template <int D, bool LC = false, bool PAIR3 = true, typename V>
 __device__ __forceinline__ void ldx_vertex(const V* p, V (&v)[D]) {
   if constexpr (D == 2 && !LC && std::is_same<V, float>::value) {
     const float2 t = __ldcg(reinterpret_cast<const float2*>(p));
@@ -143,6 +144,22 @@ __device__ __forceinline__ void ldx_vertex(const V* p, V (&v)[D]) {
     const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
     v[0] = t.x;
     v[1] = t.y;
+  } else if constexpr (D == 3 && !LC && PAIR3 && (std::is_same<V, float>::value || std::is_same<V, double>::value)) {
+    // 3 values: a pair on its 2-value boundary and a single (the vectors
+    // start on a 256-byte boundary, so the parity of the element index says
+    // which pair is aligned)
+    using V2 = typename std::conditional<std::is_same<V, float>::value, float2, double2>::type;
+    if (((reinterpret_cast<uintptr_t>(p) / sizeof(V)) & 1) == 0) {
+      const V2 t = __ldcg(reinterpret_cast<const V2*>(p));
+      v[0] = t.x;
+      v[1] = t.y;
+      v[2] = __ldcg(p + 2);
+    } else {
+      v[0] = __ldcg(p);
+      const V2 t = __ldcg(reinterpret_cast<const V2*>(p + 1));
+      v[1] = t.x;
+      v[2] = t.y;
+    }
   } else {
 #pragma unroll
     for (int a = 0; a < D; ++a) v[a] = ldx<LC>(p + a);
@@ -370,7 +387,7 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
   for (int p = 0; p < NPF; ++p) {
     if (st.cj[p] >= 0) {
       V xj[D];
-      ldx_vertex<D, LC>((const V*)L.x + (long long)st.cj[p] * D, xj);
+      ldx_vertex<D, LC, false>((const V*)L.x + (long long)st.cj[p] * D, xj);
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -388,7 +405,7 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
     V blk[D * D];
     const int j = seg_entry<D, V, S>(st.sg, e, ciA, offA, nA, ciB, offB, nB, blk);
     V xj[D];
-    ldx_vertex<D, LC>((const V*)L.x + (long long)j * D, xj);
+    ldx_vertex<D, LC, false>((const V*)L.x + (long long)j * D, xj);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll

@@ -2,7 +2,8 @@
 // device, with P = P_s (x) I_d and the rows of dead fine dofs masked.
 //
 // Pattern: the structural block product of P_s^T pattern(A_l) P_s plus the
-// diagonal (pairs (I, J) generated per fine vertex, radix sorted, made unique).
+// diagonal (pairs (I, J) generated per fine vertex, each fine vertex's coarse
+// columns made unique locally first, then radix sorted and made unique).
 // Values: one warp per coarse row I sums, in ascending fine index i and then
 // ascending block k of row i, w_iI (M A_l M)_ij w_jJ into its row -- a fixed
 // order, so the result is deterministic.  Coarse dofs whose masked column of
@@ -11,13 +12,47 @@
 
 namespace vasmg {
 
+// Coarse columns a fine row i reaches: the union over the blocks k of A_l's
+// row i of the columns of P's row j_k.  Up to GAL_UNION of them are collected,
+// sorted and made unique in thread-local storage, so that each (I, J) pair is
+// emitted once per fine row; a row with a longer candidate list emits its
+// list as it is (the global sort and unique below remove the repeats either
+// way, so the pattern is the same).
+constexpr int GAL_UNION = 128;
+
+__device__ __forceinline__ int gal_row_union(const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                                             const int32_t* __restrict__ prp, const int32_t* __restrict__ pci,
+                                             i64 i, int32_t* cols) {
+  int n = 0;
+  for (int32_t k = arp[i]; k < arp[i + 1]; ++k) {
+    const int32_t j = aci[k];
+    for (int32_t b = prp[j]; b < prp[j + 1]; ++b) {
+      if (n == GAL_UNION) return -1;
+      // insertion into the sorted prefix, skipping a repeat
+      const int32_t J = pci[b];
+      int p = n;
+      while (p > 0 && cols[p - 1] > J) --p;
+      if (p > 0 && cols[p - 1] == J) continue;
+      for (int q = n; q > p; --q) cols[q] = cols[q - 1];
+      cols[p] = J;
+      ++n;
+    }
+  }
+  return n;
+}
+
 __global__ void gal_count_kernel(const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
-                                 const int32_t* __restrict__ prp, i64 nf, long long* __restrict__ cnt) {
+                                 const int32_t* __restrict__ prp, const int32_t* __restrict__ pci, i64 nf,
+                                 long long* __restrict__ cnt) {
+  int32_t cols[GAL_UNION];
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += (i64)gridDim.x * blockDim.x) {
-    long long s = 0;
-    for (int32_t k = arp[i]; k < arp[i + 1]; ++k) {
-      const int32_t j = aci[k];
-      s += prp[j + 1] - prp[j];
+    long long s = gal_row_union(arp, aci, prp, pci, i, cols);
+    if (s < 0) {
+      s = 0;
+      for (int32_t k = arp[i]; k < arp[i + 1]; ++k) {
+        const int32_t j = aci[k];
+        s += prp[j + 1] - prp[j];
+      }
     }
     cnt[i] = s * (long long)(prp[i + 1] - prp[i]);
   }
@@ -26,13 +61,19 @@ __global__ void gal_count_kernel(const int32_t* __restrict__ arp, const int32_t*
 __global__ void gal_pairs_kernel(const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                                  const int32_t* __restrict__ prp, const int32_t* __restrict__ pci, i64 nf,
                                  const long long* __restrict__ off, u64* __restrict__ keys) {
+  int32_t cols[GAL_UNION];
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += (i64)gridDim.x * blockDim.x) {
     long long o = off[i];
+    const int nu = gal_row_union(arp, aci, prp, pci, i, cols);
     for (int32_t a = prp[i]; a < prp[i + 1]; ++a) {
       const u64 I = (uint32_t)pci[a];
-      for (int32_t k = arp[i]; k < arp[i + 1]; ++k) {
-        const int32_t j = aci[k];
-        for (int32_t b = prp[j]; b < prp[j + 1]; ++b) keys[o++] = (I << 32) | (uint32_t)pci[b];
+      if (nu >= 0) {
+        for (int q = 0; q < nu; ++q) keys[o++] = (I << 32) | (uint32_t)cols[q];
+      } else {
+        for (int32_t k = arp[i]; k < arp[i + 1]; ++k) {
+          const int32_t j = aci[k];
+          for (int32_t b = prp[j]; b < prp[j + 1]; ++b) keys[o++] = (I << 32) | (uint32_t)pci[b];
+        }
       }
     }
   }
@@ -146,7 +187,8 @@ void setup_galerkin(Ctx& c, int l) {
   DevBuf<long long> cnt;
   cnt.alloc(f.nv + 1, s);
   cnt.zero();
-  gal_count_kernel<<<grid_for(f.nv, 256), 256, 0, s>>>(f.rp.get(), f.ci.get(), f.prp.get(), f.nv, cnt.get());
+  gal_count_kernel<<<grid_for(f.nv, 256), 256, 0, s>>>(f.rp.get(), f.ci.get(), f.prp.get(), f.pci.get(), f.nv,
+                                                        cnt.get());
   check_launch("gal_count");
   scan_exclusive_i64((const i64*)cnt.get(), (i64*)cnt.get(), f.nv + 1, s);
   const i64 m = fetch(cnt.get() + f.nv, s);

@@ -2025,6 +2025,16 @@ struct Engine : EngineBase {
       cudaStream_t s = c->stream;
       dn = (int)(c->S[kd].nv * D);
       dld = (dn + 3) / 4 * 4;
+      {
+        // the tail stages b_kd in shared memory beside its levels' vectors
+        TailArgs<V> probe;
+        const size_t need = fill_tail_args(probe, lt, ls) + sizeof(V) * (size_t)dld;
+        if (need > (size_t)TAIL_SMEM_MAX) {
+          kd = -1;
+          dn = 0;
+          return;
+        }
+      }
       if (dm.n != (i64)dn * dld) dm.alloc((i64)dn * dld, s);
       dm.zero();
       DevBuf<double> ys;

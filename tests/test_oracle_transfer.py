@@ -160,3 +160,26 @@ def test_level_count_merges_to_root(oracle_mod):
     depths = [int(o.cells(l)[:, 0].max()) for l in range(1, L)]
     # each merge removes exactly the deepest layer (Sec. 3.1.2)
     assert depths == list(range(depths[0], -1, -1))
+
+
+@pytest.mark.parametrize("dim,n,seed", [(2, 14, 7), (2, 19, 9), (3, 6, 8)])
+def test_coarse_levels_keep_the_rigid_body_modes(oracle_mod, dim, n, seed):
+    """Without Dirichlet data A_0 annihilates the rigid-body modes, and P
+    reproduces linear fields exactly, so every Galerkin level
+    A_{l+1} = P^T A_l P annihilates the rigid modes evaluated at its own
+    vertices (translations and rotations are linear in the coordinates)."""
+    from tests.helpers import rigid_modes
+
+    p = _prob(dim, n, seed)
+    p["dirichlet_dofs"] = np.zeros(0, dtype=np.int64)
+    p.pop("dirichlet_values", None)
+    o = oracle_mod.Oracle(p)
+    assert o.num_levels >= 3
+    for l in range(o.num_levels):
+        rp, ci, v = o.operator(l)
+        A = dense_from_bsr(rp, ci, v, dim)
+        assert not o.dead(l).any()
+        X = _level_coords(o, l, dim)
+        for t in rigid_modes(X):
+            r = np.linalg.norm(A @ t) / (np.linalg.norm(A) * np.linalg.norm(t))
+            assert r <= 1e-12, (l, r)

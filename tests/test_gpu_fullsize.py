@@ -136,3 +136,43 @@ def test_full_size_workload(built, name, precision, check_levels):
         assert abs(true_rel - st.rel_res) <= 1e-9
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("dim,n", [(2, 300), (3, 32)])
+def test_galerkin_levels_keep_rigid_modes_large(built, dim, n):
+    """At sizes the full oracle does not reach: without Dirichlet data every
+    Galerkin level the device builds annihilates the rigid-body modes at its
+    own vertices (P reproduces linear fields, A_0 annihilates them) -- on its
+    live rows.  A coarse dof that no fine dof interpolates from with a
+    nonzero weight is dead and carries an identity row, which the rigid modes
+    are not in the kernel of."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import norm as sparse_norm
+
+    from tests.helpers import rigid_modes
+
+    prob = meshgen.make_problem(None, dim=dim, n=n, jitter=0.2 if dim == 2 else 0.15, seed=90 + n)
+    prob["dirichlet_dofs"] = np.zeros(0, dtype=np.int64)
+    prob.pop("dirichlet_values", None)
+    s = vasmg.Solver(prob, precision="fp64", stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        box = s.export(vasmg.EXPORT_BOX, 0, np.float64)
+        K = K_of(dim)
+        assert s.num_levels >= 4
+        for l in range(s.num_levels):
+            rp = s.export(vasmg.EXPORT_A_RP, l, np.int64)
+            ci = s.export(vasmg.EXPORT_A_CI, l, np.int32)
+            v = s.export(vasmg.EXPORT_A_V, l, np.float64).reshape(-1, dim, dim)
+            A = sp.bsr_matrix((v, ci, rp), shape=((rp.size - 1) * dim, (rp.size - 1) * dim)).tocsr()
+            if l == 0:
+                X = np.asarray(prob["coords"], dtype=np.float64)
+            else:
+                q = deinterleave(s.export(vasmg.EXPORT_LATTICE, l, np.uint64), dim, K + 1).astype(np.float64)
+                X = box[0] + (box[1] - box[0]) * q / 2.0 ** K
+            scale = sparse_norm(A)
+            live = ~s.export(vasmg.EXPORT_DEAD, l, np.uint8).astype(bool)
+            for t in rigid_modes(X):
+                r = np.linalg.norm((A @ t)[live]) / (scale * np.linalg.norm(t))
+                assert r <= 1e-12, (l, r)
+    finally:
+        s.close()

@@ -138,6 +138,25 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _check_vec(a, n, name):
+    """A vector argument must be a contiguous float64 numpy array or torch
+    tensor of exactly n entries (the library reads / writes n doubles)."""
+    if hasattr(a, "data_ptr"):
+        import torch
+
+        if a.dtype != torch.float64:
+            raise TypeError(f"{name} must be float64, got {a.dtype}")
+        size = a.numel()
+    elif isinstance(a, np.ndarray):
+        if a.dtype != np.float64:
+            raise TypeError(f"{name} must be float64, got {a.dtype}")
+        size = a.size
+    else:
+        raise TypeError(f"{name} must be a numpy array or a torch tensor, got {type(a).__name__}")
+    if size != n:
+        raise ValueError(f"{name} has {size} entries, expected {n}")
+
+
 def _check(rc, where, allow_not_converged=False):
     if rc == VASMG_OK or (allow_not_converged and rc == VASMG_NOT_CONVERGED):
         return rc
@@ -317,9 +336,14 @@ class Solver:
         return vasmg_export(self.h, what, level, dtype)
 
     def assemble_load(self, f, F):
+        if np.asarray(f).size != self.dim:
+            raise ValueError(f"body force has {np.asarray(f).size} components, expected {self.dim}")
+        _check_vec(F, self.n, "F")
         vasmg_assemble_load(self.h, f, F)
 
     def solve(self, F, U, tol=1e-6, history_cap=0):
+        _check_vec(F, self.n, "F")
+        _check_vec(U, self.n, "U")
         return vasmg_solve(self.h, F, U, tol, history_cap)
 
     def apply(self, op, level, x, y):

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -80,3 +81,22 @@ def test_struct_layouts_match_header():
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     assert sizes == [C.sizeof(vasmg.vasmg_problem), C.sizeof(vasmg.vasmg_options), C.sizeof(vasmg.vasmg_stats),
                      C.sizeof(vasmg.vasmg_server_opts), C.sizeof(vasmg.vasmg_request_stats)]
+
+
+def test_vector_arguments_are_checked_before_the_call():
+    """Solver.solve / assemble_load pass raw pointers: a vector of another
+    dtype or length is refused in Python, before the library reads it."""
+    import torch
+
+    from paper_2505_09064_gb300 import vasmg
+
+    vasmg._check_vec(np.zeros(6), 6, "F")
+    vasmg._check_vec(torch.zeros(6, dtype=torch.float64), 6, "F")
+    with pytest.raises(TypeError):
+        vasmg._check_vec(np.zeros(6, dtype=np.float32), 6, "F")
+    with pytest.raises(TypeError):
+        vasmg._check_vec(torch.zeros(6, dtype=torch.float32), 6, "F")
+    with pytest.raises(ValueError):
+        vasmg._check_vec(np.zeros(5), 6, "U")
+    with pytest.raises(TypeError):
+        vasmg._check_vec([0.0] * 6, 6, "U")

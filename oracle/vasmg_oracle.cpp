@@ -1,8 +1,9 @@
 // V-ASMG-PCG oracle (arXiv 2505.09064) -- TEST INFRASTRUCTURE ONLY.
 //
 // A plain, slow FP64 CPU implementation of what the solve path computes,
-// single-threaded as built by default.  Only the test-suite, the smoke check and the CPU-baseline leg of
-// the benchmark may load it; the library never does.  It shares no code with
+// single-threaded as built by default.  Only the test-suite, the smoke check
+// and the CPU-baseline leg of the benchmark may load it; the library never
+// does.  It shares no code with
 // the CUDA path: every step is written here from the paper's description, in
 // the paper's order, with no blocking, fusion or reordering.  Build flags keep
 // IEEE semantics (-O2 -ffp-contract=off) so the geometric steps round exactly

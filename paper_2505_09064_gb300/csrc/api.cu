@@ -162,7 +162,8 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
     udir[g] = pb->dirichlet_values ? pb->dirichlet_values[k] : 0.0;
     if (pb->dirichlet_values && pb->dirichlet_values[k] != 0.0) c.has_dir_values = true;
   }
-  for (int64_t i = 0; i < c.n; ++i) VASMG_CHECK(std::isfinite(pb->coords[i]), VASMG_ERR_INVALID_ARG, "non-finite coordinate");
+  for (int64_t i = 0; i < c.n; ++i)
+    VASMG_CHECK(std::isfinite(pb->coords[i]), VASMG_ERR_INVALID_ARG, "non-finite coordinate");
   c.X.alloc(c.n, s);
   c.X.upload(pb->coords, c.n);
   c.E.alloc(c.ne * (d + 1), s);

@@ -100,7 +100,9 @@ void scan_exclusive(const T* in, T* out, i64 n, cudaStream_t s) {
   check_launch("scan_apply");
 }
 
-void scan_exclusive_i64(const i64* in, i64* out, i64 n, cudaStream_t s) { scan_exclusive<long long>((const long long*)in, (long long*)out, n, s); }
+void scan_exclusive_i64(const i64* in, i64* out, i64 n, cudaStream_t s) {
+  scan_exclusive<long long>((const long long*)in, (long long*)out, n, s);
+}
 void scan_exclusive_i32(const int32_t* in, int32_t* out, i64 n, cudaStream_t s) { scan_exclusive<int>(in, out, n, s); }
 
 // ------------------------------------------------------------------ radix sort

@@ -821,7 +821,8 @@ __device__ __forceinline__ void one_cta_down(const TailArgs<V>& A, V* sm, int lf
   for (int l = lfrom; l < lto; ++l) {
     const TL<V> L = shared_level<D, V>(A, l, sm);
     tail_sweep<D, G, V, S, 0, true>(L, g, ng, lane, CtaSync());
-    for (int base = 0; base < L.nv; base += ng) row_pass<D, G, V, S, 2, TL<V>, true>(L, base + g, base + g < L.nv, lane);
+    for (int base = 0; base < L.nv; base += ng)
+      row_pass<D, G, V, S, 2, TL<V>, true>(L, base + g, base + g < L.nv, lane);
     __syncthreads();
     for (int I = tid; I < L.nvc; I += NT) restrict_row<D, V, TL<V>, true>(L, I);
     __syncthreads();
@@ -2473,7 +2474,9 @@ int solve_dev(Ctx& c, const double* F_dev, double* U_dev, double tol, vasmg_stat
   return c.eng->solve(c, F_dev, U_dev, tol, st);
 }
 
-void apply_op(Ctx& c, int op, int level, const double* x_dev, double* y_dev) { c.eng->apply(c, op, level, x_dev, y_dev); }
+void apply_op(Ctx& c, int op, int level, const double* x_dev, double* y_dev) {
+  c.eng->apply(c, op, level, x_dev, y_dev);
+}
 
 double time_kernel(Ctx& c, int which, int level, int reps, double* bytes) {
   return c.eng->time(c, which, level, reps, bytes);

@@ -44,3 +44,23 @@ def test_parallel_oracle_bitwise_equal(name):
         nc = o1.level_info(l + 1)[0] * p["dim"]
         ec = rs.uniform(nc, -1.0, 1.0)
         assert np.array_equal(o1.prolong_add(l, ec, b), o4.prolong_add(l, ec, b))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_parallel_oracle_cycle_variants_bitwise_equal(name):
+    """The W-cycle, the additive form and the lexicographic smoother go
+    through the same parallel loops; both builds still agree bit for bit."""
+    p = meshgen.make_problem(None, **CASES[name])
+    o1 = oracle.Oracle(p)
+    o4 = oracle.Oracle(p, threads=4)
+    F = o1.assemble_load(p["body_force"])
+    F[p["dirichlet_dofs"]] = 0.0
+    for kw, smoother in [(dict(gamma=2), "multicolour"), (dict(additive=True), "multicolour"),
+                         (dict(gamma=1), "lexicographic")]:
+        for o in (o1, o4):
+            o.set_cycle(**kw)
+            o.set_smoother(smoother)
+        U1, it1, rr1, st1, _ = o1.solve(F, tol=1e-8)
+        U4, it4, rr4, st4, _ = o4.solve(F, tol=1e-8)
+        assert st1 == st4 == 0 and it1 == it4 and rr1 == rr4
+        assert np.array_equal(U1, U4), (kw, smoother)

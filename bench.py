@@ -1,21 +1,25 @@
 """Benchmark: V-ASMG-PCG MDOF*iter/s to 1e-6 relative residual on GB300.
 
-Workload: 2D plane strain on the unit square, 1024x1024 jittered P1 triangle
-mesh (2,097,152 dofs, 2,095,104 free), E in {1, 100} on an 8x8 checkerboard,
-nu = 0.3, left edge clamped, body force (0,-1).  One step = one full solve
-(every row of the hot path: FP64 SpMV + CG updates + V-cycle with multicolour
-block GS, residual, restriction, coarsest Cholesky solve, prolongation) from
-U0 = 0 to ||r||/||F|| < 1e-6.  The headline runs the FP32 V-cycle inside the
-FP64 CG; the plain FP64 path is timed beside it.
+Headline workload (the largest single-GPU configuration): 3D linear
+elasticity on a 128^3 vertex grid graded toward one corner (spacing ratio 16
+per axis), 6 Kuhn tetrahedra per hex (6,291,456 dofs, 6,242,304 free), E = 1,
+nu = 0.45, face x = 0 clamped, body force (0,0,-1); BF16 operator values in the
+smoother, FP32 transfers and coarse operators, FP64 outer CG and coarsest
+Cholesky.  One step = one full solve (every row of the hot path: FP64 SpMV +
+CG updates + V-cycle with multicolour block GS, residual, restriction,
+coarsest Cholesky solve, prolongation) from U0 = 0 to ||r||/||F|| < 1e-6.
+The plain FP64 path on the same mesh is timed beside it, and so are the
+other configurations (2D 64^2 FP64; 2D 1024^2 1:100 checkerboard, FP32
+V-cycle and FP64; 3D 64^3 FP32 V-cycle), each with iterations and ms per solve.
 
 value = sum(n_free * iterations) / device time / 1e6, inputs resident in HBM.
 e2e   = the same through vasmg_solve with pinned host F and U (H2D + D2H in
         the timed region).
-The operators (268 MB FP64 level-0 matrix alone) exceed the 129 MB L2, so no
-explicit flush is needed between timed steps.
+The operators (1.3 GB of level-0 FP64 blocks alone) exceed the 129 MB L2, so
+no explicit flush is needed between timed steps.
 
 --impl reference times the CPU oracle (single thread) on a bounded sample of
-the same workload.
+the same workload: the same recipe at 32^3 vertices.
 """
 from __future__ import annotations
 
@@ -32,9 +36,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "square1024_checker"
+WORKLOAD = "cube128_graded"
+# V-cycle precision of each workload's configuration
+DEFAULT_PRECISION = {"cube128_graded": "bf16", "cube64": "fp32", "square1024_checker": "fp32", "square64": "fp64"}
 TAIL_NV = 20000         # levels this small run inside the single cluster tail launch
-SAMPLE_N = 192          # CPU sample: same recipe at 192x192 vertices
+# CPU sample: the same recipe at this many vertices per side (a full oracle
+# solve takes about 10 s on one core)
+SAMPLE_N = {"cube128_graded": 32, "cube64": 32, "square1024_checker": 192, "square64": 64}
 # DRAM bytes (read + write) of one launch from an ncu capture of the current
 # kernel (profiles/); absent when the kernel changed after the capture
 TRAFFIC = {
@@ -60,7 +68,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "bf16"],
+                    help="V-cycle precision (default: the workload's configuration)")
+    ap.add_argument("--no-others", action="store_true", help="skip the other workloads' lines")
+    ap.add_argument("--fp64-peak", action="store_true", help="only measure the FP64 FMA rate and print it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="lanes per row by rule (setup then launches no timing runs; for launch-indexed profiles)")
@@ -70,7 +81,10 @@ def parse():
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no per-kernel roofline timing, e2e, FP64 path or CPU "
                          "baseline); used for profiler launch lists")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precision is None:
+        args.precision = DEFAULT_PRECISION.get(args.workload, "fp32")
+    return args
 
 
 def reduce_over_ranks(ms: float, work: float, device=None):
@@ -154,16 +168,43 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def cpu_oracle_run(n: int, steps: int, threads: int = 1):
-    """Time the CPU oracle's solve on the same recipe at n x n vertices.
-    threads > 1 runs the oracle's OpenMP build (same bits, independent row
-    loops on that many threads).  Returns (values, free dofs, threads used)."""
-    import oracle
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def sample_problem(workload: str, n: int):
+    """The workload's recipe (mesh, material, boundary conditions, load) at n
+    vertices per side."""
     from paper_2505_09064_gb300 import meshgen
 
-    cfg = dict(meshgen.WORKLOADS[WORKLOAD])
-    prob = meshgen.make_problem(None, dim=2, n=n, jitter=cfg["jitter"], seed=cfg["seed"], E=cfg["E"],
-                                nu=cfg["nu"], checker=cfg["checker"])
+    cfg = dict(meshgen.WORKLOADS[workload])
+    return meshgen.make_problem(None, dim=cfg["dim"], n=n, jitter=cfg["jitter"], seed=cfg["seed"], E=cfg["E"],
+                                nu=cfg["nu"], checker=cfg["checker"], graded=cfg["graded"])
+
+
+def cpu_oracle_run(workload: str, n: int, steps: int, threads: int = 1):
+    """Time the CPU oracle's solve on the workload's recipe at n vertices per
+    side.  threads > 1 runs the oracle's OpenMP build (same bits, independent
+    row loops on that many threads).  Returns (values, free dofs, threads used)
+    with values = [(MDOF*iter/s, iterations, seconds)] per solve."""
+    import oracle
+
+    prob = sample_problem(workload, n)
     o = oracle.Oracle(prob, threads=threads)
     F = o.assemble_load(prob["body_force"])
     nfree = F.size - prob["dirichlet_dofs"].size
@@ -264,21 +305,39 @@ def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    vals, nfree, _ = cpu_oracle_run(SAMPLE_N, args.warmup + args.steps)
+    n = SAMPLE_N.get(args.workload, 32)
+    vals, nfree, _ = cpu_oracle_run(args.workload, n, args.warmup + args.steps)
     timed = vals[args.warmup:] if len(vals) > args.warmup else vals
     total_work = sum(v[0] * v[2] for v in timed)
     total_t = sum(v[2] for v in timed)
     value = total_work / total_t
-    sample = f"{WORKLOAD} recipe at {SAMPLE_N}x{SAMPLE_N} vertices ({nfree} free dofs), full solve to {TOL}, 1 thread"
+    side = f"{n}^3" if args.workload.startswith("cube") else f"{n}x{n}"
+    sample = (f"{args.workload} recipe at {side} vertices ({nfree} free dofs), one full solve to {TOL} per step, "
+              f"1 thread, CPU {cpu_model()}")
     line = {"impl": "reference", "metric": "V-ASMG-PCG MDOF*iter/s to 1e-6 rel. residual", "value": value,
             "unit": "MDOF*iter/s", "n_gpus": args.gpus, "steps": len(timed), "warmup": args.warmup,
             "ms_per_step": 1e3 * total_t / len(timed), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD} (CPU oracle sample {SAMPLE_N}x{SAMPLE_N})",
-                       "iterations": timed[0][1]},
-            "cpu_baseline": {"value": value, "unit": "MDOF*iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": f"{args.workload} (CPU oracle sample {side})", "iterations": timed[0][1]},
+            "cpu_baseline": {"value": value, "unit": "MDOF*iter/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": "MDOF*iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fp64_roof(vasmg):
+    """Measured FP64 FMA rate (TFLOP/s) of this GPU, the arithmetic roof of the
+    FP64 kernels."""
+    tf, ms = vasmg.vasmg_probe_fp64_rate()
+    return {"tflops": tf, "kernel_ms": ms, "how": "independent FMA chains on every SM, CUDA events, mean of 5 launches"}
+
+
+def spmv64_flops(s, vasmg):
+    """Algorithmic FP64 flops of one level-0 SpMV with the p.q product: 2 d^2
+    per stored block (diagonal included) + 2 per dof."""
+    d = 2 if s.dim == 2 else 3
+    nv, nnzb, _ = vasmg.vasmg_level_info(s.h, 0)
+    return 2.0 * d * d * nnzb + 2.0 * nv * d
 
 
 def ours(args):
@@ -294,12 +353,15 @@ def ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream().cuda_stream
+    if args.fp64_peak:
+        if rank == 0:
+            print(json.dumps({"fp64_fma": fp64_roof(vasmg)}), flush=True)
+        return
 
-    prob = meshgen.make_problem(args.workload)
-    n = prob["coords"].shape[0] * prob["dim"]
-    nfree = n - prob["dirichlet_dofs"].size
-
-    def run_solver(precision, threshold=0):
+    def make(workload, precision, threshold=0):
+        prob = meshgen.make_problem(workload)
+        n = prob["coords"].shape[0] * prob["dim"]
+        nfree = n - prob["dirichlet_dofs"].size
         s = vasmg.Solver(prob, precision=precision, stream=stream, use_graph=not args.no_graph,
                          threshold=threshold, autotune=not args.no_autotune)
         F = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -308,7 +370,7 @@ def ours(args):
         for _ in range(args.warmup):
             s.solve(F, U, TOL)
         torch.cuda.synchronize()
-        return s, F, U
+        return s, F, U, n, nfree
 
     def timed(s, F, U, steps):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -329,8 +391,24 @@ def ours(args):
             torch.distributed.barrier()
         return ms, iters, launches, st
 
-    # headline precision
-    s, F, U = run_solver(args.precision)
+    def line_of(workload, precision, steps, threshold=0, keep=False):
+        """A secondary line: value, iterations and ms per solve of one
+        configuration (timed alone, CUDA events)."""
+        s2, F2, U2, n2, nf2 = make(workload, precision, threshold)
+        ms2, it2, _, st2 = timed(s2, F2, U2, steps)
+        nb = [vasmg.vasmg_level_info(s2.h, l)[1] for l in range(vasmg.vasmg_num_levels(s2.h))]
+        out = {"value": nf2 * sum(it2) / (ms2 / 1e3) / 1e6, "unit": "MDOF*iter/s", "precision": precision,
+               "iterations": it2[0], "ms_per_solve": ms2 / len(it2), "solves": len(it2), "dofs": n2,
+               "free_dofs": nf2, "setup_ms": st2.setup_ms, "levels": len(nb), "op_complexity": sum(nb) / nb[0]}
+        if threshold:
+            out["leaf_threshold"] = threshold
+        if keep:
+            return out, (s2, U2)
+        s2.close()
+        return out, None
+
+    # headline
+    s, F, U, n, nfree = make(args.workload, args.precision)
     clocks = ClockSampler(local)
     clocks.start()
     ms, iters, launches, st = timed(s, F, U, args.steps)
@@ -342,7 +420,10 @@ def ours(args):
             print(json.dumps({"metric": "V-ASMG-PCG MDOF*iter/s to 1e-6 rel. residual", "value": value,
                               "unit": "MDOF*iter/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                               "ms_per_step": ms / args.steps, "iterations": iters[0], "gpu_launches": launches,
-                              "graph": not args.no_graph, "solve_only": True, "clocks": clk}), flush=True)
+                              "graph": not args.no_graph, "solve_only": True, "workload": args.workload,
+                              "precision": args.precision, "clocks": clk,
+                              "lanes_per_row": [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)]}),
+                  flush=True)
         s.close()
         return
     # roofline: every kernel of one PCG iteration timed alone on the library's
@@ -367,6 +448,13 @@ def ours(args):
     top = max(kernels, key=lambda k: kernels[k][0])
     k_ms, k_bytes = kernels[top]
     achieved = k_bytes / (k_ms / 1e3) / 1e9
+    f64 = fp64_roof(vasmg)
+    sp_ms, sp_bytes = kernels["spmv64_sell"]
+    sp_flops = spmv64_flops(s, vasmg)
+    spmv_roofs = {"ms": sp_ms, "bytes": sp_bytes, "gbs": sp_bytes / (sp_ms / 1e3) / 1e9,
+                  "hbm_frac": sp_bytes / (sp_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "flops": sp_flops,
+                  "tflops": sp_flops / (sp_ms / 1e3) / 1e12,
+                  "fp64_frac": sp_flops / (sp_ms / 1e3) / 1e12 / f64["tflops"]}
     # e2e: pinned host F and U, copies inside the timed region
     Fh = F.cpu().pin_memory()
     Uh = torch.zeros_like(Fh).pin_memory()
@@ -380,32 +468,43 @@ def ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_ms, e2e_work = reduce_over_ranks(e2e_s * 1e3, float(nfree * e2e_iters), dev)
     e2e = e2e_work / (e2e_ms / 1e3) / 1e6
-    # the plain FP64 path on the same workload
+    levels = [vasmg.vasmg_level_info(s.h, l) for l in range(vasmg.vasmg_num_levels(s.h))]
+    lanes = [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)]
+    dense = [int(v) for v in s.export(vasmg.EXPORT_DENSE, 0, np.int64)]
+    setup_ms = st.setup_ms
+    op_cx = st.op_complexity
+    # the plain FP64 path on the same workload, with the headline solution's
+    # distance from it (the FP64 path matches the FP64 oracle to 1e-10 on the
+    # parity cases)
     fp64 = None
+    extra = max(1, min(args.steps, 3))
     if args.precision != "fp64":
-        s64, F64, U64 = run_solver("fp64")
-        ms64, it64, _, _ = timed(s64, F64, U64, max(1, args.steps))
-        # the headline solution against the FP64 path's (which matches the
-        # FP64 oracle to 1e-10 on the parity cases): max-norm relative error
-        err = float((U - U64).abs().max().item() / max(U64.abs().max().item(), 1e-300))
-        fp64 = {"value": nfree * sum(it64) / (ms64 / 1e3) / 1e6, "iterations": it64[0],
-                "ms_per_solve": ms64 / len(it64), "rel_error_of_headline_solution": err}
+        fp64, keep = line_of(args.workload, "fp64", extra, keep=True)
+        s64, U64 = keep
+        fp64["rel_error_of_headline_solution"] = float((U - U64).abs().max().item() /
+                                                       max(U64.abs().max().item(), 1e-300))
+        fp64["spmv64"] = {"ms": vasmg.vasmg_time_kernel(s64.h, vasmg.KERNEL_SPMV64, 0, 20)[0]}
         s64.close()
-    # the same solve with a coarser region tree (leaf threshold 8, not the
-    # paper's 4 in 2D): fewer, sparser coarse levels for a few more iterations
-    variants = None
-    if args.workload.startswith("square") and world == 1:
-        sT, FT, UT = run_solver(args.precision, threshold=8)
-        msT, itT, _, _ = timed(sT, FT, UT, max(1, args.steps))
-        nbT = [vasmg.vasmg_level_info(sT.h, l)[1] for l in range(vasmg.vasmg_num_levels(sT.h))]
-        variants = {"leaf_threshold_8": {"value": nfree * sum(itT) / (msT / 1e3) / 1e6, "unit": "MDOF*iter/s",
-                                         "iterations": itT[0], "ms_per_solve": msT / len(itT),
-                                         "op_complexity": sum(nbT) / nbT[0], "levels": len(nbT)}}
-        sT.close()
+    # the other configurations, each on its own
+    others = None
+    if not args.no_others and world == 1:
+        s.close()
+        s = None
+        others = {}
+        for wl in ("square64", "square1024_checker", "cube64"):
+            if wl == args.workload:
+                continue
+            pr = DEFAULT_PRECISION[wl]
+            entry = {pr: line_of(wl, pr, extra)[0]}
+            if pr != "fp64":
+                entry["fp64"] = line_of(wl, "fp64", extra)[0]
+            if wl == "square1024_checker":
+                # leaf threshold 8 instead of the paper's 4: fewer, sparser coarse levels
+                entry["leaf_threshold_8"] = line_of(wl, pr, extra, threshold=8)[0]
+            others[wl] = entry
     serving = None
     if not args.no_serving:
         serving = serving_run(stream)
-    levels = [vasmg.vasmg_level_info(s.h, l) for l in range(vasmg.vasmg_num_levels(s.h))]
     line = {"metric": "V-ASMG-PCG MDOF*iter/s to 1e-6 rel. residual", "value": value, "unit": "MDOF*iter/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -413,12 +512,11 @@ def ours(args):
                 args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "dofs": n, "free_dofs": nfree, "iterations": iters[0],
-                       "precision": args.precision, "tol": TOL, "levels": len(levels),
-                       "level_vertices": [lv[0] for lv in levels], "level_blocks": [lv[1] for lv in levels],
-                       "level_colours": [lv[2] for lv in levels], "op_complexity": st.op_complexity,
-                       "lanes_per_row": [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)],
-                       "dense_level": [int(v) for v in s.export(vasmg.EXPORT_DENSE, 0, np.int64)],
-                       "setup_ms": st.setup_ms, "l2": "operators > L2 (no flush needed)",
+                       "ms_per_solve": ms / args.steps, "precision": args.precision, "tol": TOL,
+                       "levels": len(levels), "level_vertices": [lv[0] for lv in levels],
+                       "level_blocks": [lv[1] for lv in levels], "level_colours": [lv[2] for lv in levels],
+                       "op_complexity": op_cx, "lanes_per_row": lanes, "dense_level": dense,
+                       "setup_ms": setup_ms, "l2": "operators > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "limiter": "latency" if top.startswith("tail") else "latency/HBM",
                          "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -426,26 +524,33 @@ def ours(args):
                          "kernel": top, "peak_source": peak_src, "launch_ms": k_ms, "algorithmic_bytes": k_bytes,
                          "launches": {k: {"ms": v[0], "bytes": v[1], "gbs": v[1] / (v[0] / 1e3) / 1e9}
                                       for k, v in kernels.items()},
-                         "vcycle": {"ms": vc_ms, "bytes": vc_bytes, "gbs": vc_bytes / (vc_ms / 1e3) / 1e9}},
+                         "vcycle": {"ms": vc_ms, "bytes": vc_bytes, "gbs": vc_bytes / (vc_ms / 1e3) / 1e9},
+                         "fp64_fma": f64, "spmv64": spmv_roofs},
             "e2e": {"value": e2e, "unit": "MDOF*iter/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
-            "gpu_launches": launches, "clocks": clk, "fp64_path": fp64, "variants": variants, "serving": serving}
+            "gpu_launches": launches, "clocks": clk, "fp64_path": fp64, "other_workloads": others,
+            "serving": serving}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        vals, nf, _ = cpu_oracle_run(SAMPLE_N, 2)
+        ns = SAMPLE_N.get(args.workload, 32)
+        side = f"{ns}^3" if args.workload.startswith("cube") else f"{ns}x{ns}"
+        model = cpu_model()
+        vals, nf, _ = cpu_oracle_run(args.workload, ns, 1)
         v = vals[-1]
         line["cpu_baseline"] = {"value": v[0], "unit": "MDOF*iter/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{WORKLOAD} recipe at {SAMPLE_N}x{SAMPLE_N} vertices ({nf} free dofs), "
-                                          f"full solve to {TOL}, {v[1]} iterations, 1 thread"}
+                                "cpu_model": model, "nproc": os.cpu_count(),
+                                "sample": f"{args.workload} recipe at {side} vertices ({nf} free dofs), "
+                                          f"one full solve to {TOL}, {v[1]} iterations, {v[2]:.1f} s, 1 thread"}
         # second CPU line: the same oracle source built with OpenMP, its
         # independent row loops on every host core (bitwise the same solve)
-        vals, nf, th = cpu_oracle_run(SAMPLE_N, 3, threads=os.cpu_count() or 1)
+        vals, nf, th = cpu_oracle_run(args.workload, ns, 2, threads=os.cpu_count() or 1)
         v = max(vals)
         line["cpu_baseline_parallel"] = {
-            "value": v[0], "unit": "MDOF*iter/s", "cores": th, "kind": "oracle, OpenMP build",
+            "value": v[0], "unit": "MDOF*iter/s", "cores": th, "kind": "oracle, OpenMP build", "cpu_model": model,
             "sample": f"as cpu_baseline, {v[1]} iterations, {th} threads (colour, y = A x and prolongation row "
-                      f"loops parallel; reductions serial), best of 3 solves"}
+                      f"loops parallel; reductions serial), best of 2 solves"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    s.close()
+    if s is not None:
+        s.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

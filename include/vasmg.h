@@ -295,30 +295,40 @@ int vasmg_apply(vasmg_handle h, int32_t op, int32_t level, const double* x, doub
  * vasmg_apply(h, VASMG_OP_COARSE, ...), which stages its vectors through
  * device buffers it allocates on every call.  Use this entry point where the
  * caller cannot allocate device memory during the call: a server whose
- * device memory is budgeted per request, or a latency-bound loop that must
+ * device memory is budgeted per request (an allocation could push it over its
+ * budget or wait on the allocator's lock), or a latency-bound loop that must
  * not enter the allocator.
  *
- * b, x    device pointers, [n] doubles each, n = dim * (vertices of the
- *         coarsest level), canonical order (dof = vertex*dim + component), as
- *         for VASMG_OP_COARSE.  b and x may be the same buffer.
+ * b, x    device (or managed) pointers on the handle's device, [n] doubles
+ *         each, n = dim * (vertices of the coarsest level), canonical order
+ *         (dof = vertex*dim + component), as for VASMG_OP_COARSE.  b and x
+ *         may be the same buffer.  The library cannot check their length.
  * stream  cudaStream_t to run on (NULL: the legacy default stream).
  *
- * The work runs asynchronously on `stream`; the call returns once it is
- * enqueued.  It reads the handle's FP64 Cholesky factor and uses a scratch
- * array of VASMG_NOALLOC_MAX_DOFS doubles in the library's static device
- * memory.  Nothing in that scratch needs to start at zero: each call writes
- * every entry it reads.
+ * The device current at the call must be the one that was current at
+ * vasmg_setup (the factor lives there).  The work runs asynchronously on
+ * `stream`; the call returns once it is enqueued.  It reads the handle's FP64
+ * Cholesky factor (every precision mode keeps one) and uses a scratch array of
+ * VASMG_NOALLOC_MAX_DOFS doubles (32 KiB) in the library's static device
+ * memory, which every device that loads the library holds until the process
+ * exits.  Nothing in that scratch needs to start at zero: each call writes
+ * every entry it reads, and the array keeps the last call's values.
  *
  * The scratch is shared by every call on the device, so two calls whose
  * kernels overlap on the GPU (e.g. issued on different streams without
  * ordering) race and give wrong results; order such calls on one stream or
- * with events.  The first call on a device looks up the scratch address with
- * cudaGetSymbolAddress; make one call before capturing a stream that will
- * contain later calls.
+ * with events.  vasmg_update_data waits for the last call's kernel before it
+ * rewrites the factor; a call issued after vasmg_update_data returns sees the
+ * new factor.  The first call on a device (and again after the device's
+ * context was reset) looks up the scratch address with cudaGetSymbolAddress,
+ * which may load the library's device code; make that first call before
+ * capturing a stream that will contain later calls.
  *
- * Returns VASMG_ERR_INVALID_ARG for NULL pointers or when n exceeds
- * VASMG_NOALLOC_MAX_DOFS (the detail string is not updated on this path),
- * VASMG_ERR_CUDA if a CUDA call fails. */
+ * Returns VASMG_ERR_INVALID_ARG for NULL pointers, for b or x not in device
+ * memory of the handle's device, when another device is current, or when n
+ * exceeds VASMG_NOALLOC_MAX_DOFS (the detail string is not updated on this
+ * path: that would allocate host memory); VASMG_ERR_CUDA if a CUDA call
+ * fails. */
 #define VASMG_NOALLOC_MAX_DOFS 4096
 int vasmg_coarse_solve_noalloc(vasmg_handle h, const double* b, double* x, void* stream);
 
@@ -339,6 +349,13 @@ enum {
                                     single cluster launch that runs the small levels */
 };
 int vasmg_time_kernel(vasmg_handle h, int32_t which, int32_t level, int32_t reps, double* ms, double* bytes);
+
+/* Measured FP64 FMA throughput of the current device, the arithmetic roof of
+ * the FP64 kernels (the outer CG's SpMV): a kernel of independent FMA chains
+ * on every SM, timed with CUDA events (one warm-up launch, five timed).
+ * *tflops = 2 * FMAs / time / 1e12; *ms (may be NULL) = one launch.  The
+ * paper has no counterpart (measurement hook). */
+int vasmg_probe_fp64_rate(double* tflops, double* ms);
 
 /* Kernels launched by the last vasmg_solve (for accounting). */
 int64_t vasmg_last_launch_count(vasmg_handle h);

@@ -38,7 +38,7 @@ int fail(const std::exception& e) {
 
 void destroy_ctx(vasmg_ctx* h) {
   cudaStream_t s = h->c.stream;
-  cudaEvent_t ev = h->c.join_ev;
+  cudaEvent_t ev = h->c.join_ev, nev = h->c.noalloc_ev;
   destroy_solver_state(h->c);
   delete h;
   if (s) {
@@ -46,39 +46,74 @@ void destroy_ctx(vasmg_ctx* h) {
     cudaStreamDestroy(s);
   }
   if (ev) cudaEventDestroy(ev);
+  if (nev) {
+    cudaEventSynchronize(nev);
+    cudaEventDestroy(nev);
+  }
 }
 
 // Scratch of vasmg_coarse_solve_noalloc: static device memory, so the call
-// never allocates.  Its device address is looked up once per device.
+// never allocates.  In host code the name is only a host-side stand-in; the
+// device address is looked up with cudaGetSymbolAddress once per device and
+// context (a context created after a reset loads the module again, and the
+// array may then sit elsewhere) and passed to the kernel.
 __device__ __align__(256) double g_noalloc_scratch[VASMG_NOALLOC_MAX_DOFS];
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kMaxDevices] = {};
+struct NoallocSlot {
+  unsigned long long ctx_id = 0;  // 0: not looked up yet
+  double* ptr = nullptr;
+};
+NoallocSlot g_noalloc_slot[kMaxDevices];
 
-// Forward and backward substitution with the FP64 Cholesky factor (canonical
-// dof order), by one warp; y is the scratch of n doubles.
+// cuCtxGetCurrent / cuCtxGetId through the runtime's driver entry points (the
+// library links the runtime statically and not libcuda): the id of the current
+// context, unique for the life of the process.  0 if unavailable.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)f;
+    cudaGetLastError();
+  });
+  if (!get_cur || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Coarsest solve into x from b (canonical dof order): copy b into the scratch,
+// substitute with the FP64 Cholesky factor (the same routine as the V-cycle's
+// coarsest solve), copy out.  One warp.
 __global__ void coarse_noalloc_kernel(const double* __restrict__ chol, const uint8_t* __restrict__ drop, int n,
                                       const double* b, double* x, double* y) {
   const int lane = threadIdx.x & 31;
   for (int t = lane; t < n; t += 32) y[t] = b[t];
   __syncwarp();
-  for (int j = 0; j < n; ++j) {
-    const double ljj = chol[(long long)j * n + j];
-    const double yj = drop[j] ? 0.0 : y[j] / ljj;
-    __syncwarp();
-    if (lane == 0) y[j] = yj;
-    for (int i = j + 1 + lane; i < n; i += 32) y[i] -= chol[(long long)i * n + j] * yj;
-    __syncwarp();
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    const double ljj = chol[(long long)j * n + j];
-    const double xj = drop[j] ? 0.0 : y[j] / ljj;
-    __syncwarp();
-    if (lane == 0) y[j] = xj;
-    for (int i = lane; i < j; i += 32) y[i] -= chol[(long long)j * n + i] * xj;
-    __syncwarp();
-  }
+  chol_substitute_warp(chol, drop, n, y);
   for (int t = lane; t < n; t += 32) x[t] = y[t];
+}
+
+// True if p is device (or managed) memory on device dev.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 double now_ms() {
@@ -144,8 +179,10 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   c.autotune = o.autotune;
   c.coarse_max_dofs = o.coarse_max_dofs;
   c.user_stream = (cudaStream_t)o.stream;
+  VASMG_CUDA(cudaGetDevice(&c.device));
   VASMG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
   VASMG_CUDA(cudaEventCreateWithFlags(&c.join_ev, cudaEventDisableTiming));
+  VASMG_CUDA(cudaEventCreateWithFlags(&c.noalloc_ev, cudaEventDisableTiming));
   join_user(c);
   c.nv = pb->n_vertices;
   c.ne = pb->n_elements;
@@ -202,6 +239,8 @@ int vasmg_update_data(vasmg_handle h, const double* lambda, const double* mu, do
   Ctx& c = h->c;
   join_user(c);
   cudaStream_t s = c.stream;
+  // a vasmg_coarse_solve_noalloc kernel still reading the factor finishes first
+  VASMG_CUDA(cudaStreamWaitEvent(s, c.noalloc_ev, 0));
   std::vector<double> lam((size_t)c.ne), mu_v((size_t)c.ne);
   for (int64_t e = 0; e < c.ne; ++e) {
     lam[e] = lambda ? lambda[e] : lambda_const;
@@ -478,18 +517,34 @@ int vasmg_coarse_solve_noalloc(vasmg_handle h, const double* b, double* x, void*
   if (n <= 0 || n > VASMG_NOALLOC_MAX_DOFS) return VASMG_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VASMG_ERR_CUDA;
+  // the factor lives on the handle's device: the kernel must run there
+  if (dev != c.device) return VASMG_ERR_INVALID_ARG;
+  if (!on_device(b, dev) || !on_device(x, dev)) return VASMG_ERR_INVALID_ARG;
   double* scratch = nullptr;
   {
+    const unsigned long long ctx = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoallocSlot& slot = g_noalloc_slot[dev];
+    if (!slot.ptr || slot.ctx_id != ctx || ctx == 0) {
       void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VASMG_ERR_CUDA;
-      g_noalloc_ptr[dev] = (double*)p;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return VASMG_ERR_CUDA;
+      }
+      slot.ptr = (double*)p;
+      slot.ctx_id = ctx;
     }
-    scratch = g_noalloc_ptr[dev];
+    scratch = slot.ptr;
   }
-  coarse_noalloc_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(c.chol.get(), c.chol_drop.get(), (int)n, b, x, scratch);
-  return cudaGetLastError() == cudaSuccess ? VASMG_OK : VASMG_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  coarse_noalloc_kernel<<<1, 32, 0, s>>>(c.chol.get(), c.chol_drop.get(), (int)n, b, x, scratch);
+  if (cudaGetLastError() != cudaSuccess) return VASMG_ERR_CUDA;
+  // vasmg_update_data waits for this before it refills the factor
+  if (cudaEventRecord(c.noalloc_ev, s) != cudaSuccess) {
+    cudaGetLastError();
+    return VASMG_ERR_CUDA;
+  }
+  return VASMG_OK;
 }
 
 int64_t vasmg_last_launch_count(vasmg_handle h) { return h ? h->c.last_launches : -1; }
@@ -519,6 +574,13 @@ const char* vasmg_error_string(int code) {
 
 // Detail of the last error on this thread (not part of the stable ABI).
 const char* vasmg_last_error_detail(void) { return g_last_error.c_str(); }
+
+int vasmg_probe_fp64_rate(double* tflops, double* ms) {
+  if (!tflops) return VASMG_ERR_INVALID_ARG;
+  VASMG_API_BEGIN
+  return probe_fp64_rate(tflops, ms);
+  VASMG_API_END
+}
 
 int vasmg_probe_wait_timeout(double* elapsed_ms) {
   VASMG_API_BEGIN

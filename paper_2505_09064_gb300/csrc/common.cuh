@@ -189,6 +189,10 @@ struct Ctx {
   cudaStream_t stream = 0;       // internal non-blocking stream owned by the handle
   cudaStream_t user_stream = 0;  // caller's stream (options.stream)
   cudaEvent_t join_ev = nullptr;
+  int device = -1;               // the device current at vasmg_setup; all of the handle's memory is there
+  // recorded on the caller's stream after each vasmg_coarse_solve_noalloc
+  // kernel; vasmg_update_data waits for it before refilling the factor
+  cudaEvent_t noalloc_ev = nullptr;
   i64 nv = 0, ne = 0, n = 0;
   double setup_ms = 0;
   // inputs
@@ -247,6 +251,7 @@ double time_kernel(Ctx& c, int which, int level, int reps, double* bytes);
 void dense_level_info(Ctx& c, int* kd, int* dn);  // the engine's dense level, (-1, 0) if none
 void lanes_info(Ctx& c, int32_t* g, int n);       // lanes per row of the region levels, 0 elsewhere
 int probe_wait_timeout(double* elapsed_ms);       // the bounded device wait run out on purpose
+int probe_fp64_rate(double* tflops, double* ms);  // FP64 FMA throughput of the current device
 void destroy_solver_state(Ctx& c);
 
 // small device helpers shared across files
@@ -316,6 +321,31 @@ __host__ __device__ inline u64 splitmix64(u64 x) {
 // block), 3 x 3 blocks as d*d planes of n values (coalesced across rows).
 __host__ __device__ inline long long block_index(int q, long long k, long long n, int dd) {
   return dd == 4 ? k * 4 + q : (long long)q * n + k;
+}
+
+// Forward and backward substitution with a dense lower Cholesky factor L
+// (row-major n x n, FP64) by one warp, in place on y[0..n): y <- L^{-T} L^{-1} y.
+// A dropped pivot (drop[j] != 0) removes direction j: y_j is set to 0 in both
+// passes.  Used by the coarsest-level solves of the V-cycle and of
+// vasmg_coarse_solve_noalloc.
+__device__ __forceinline__ void chol_substitute_warp(const double* chol, const uint8_t* drop, int n, double* y) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {
+    const double ljj = chol[(long long)j * n + j];
+    const double yj = drop[j] ? 0.0 : y[j] / ljj;
+    __syncwarp();
+    if (lane == 0) y[j] = yj;
+    for (int i = j + 1 + lane; i < n; i += 32) y[i] -= chol[(long long)i * n + j] * yj;
+    __syncwarp();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const double ljj = chol[(long long)j * n + j];
+    const double xj = drop[j] ? 0.0 : y[j] / ljj;
+    __syncwarp();
+    if (lane == 0) y[j] = xj;
+    for (int i = lane; i < j; i += 32) y[i] -= chol[(long long)j * n + i] * xj;
+    __syncwarp();
+  }
 }
 
 inline int grid_for(i64 n, int threads, int cap = 1 << 20) {

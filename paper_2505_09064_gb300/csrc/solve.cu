@@ -642,7 +642,8 @@ struct CoarseArgs {
   int n, d;
 };
 
-// Forward / backward substitution with the Cholesky factor, by one warp.
+// Forward / backward substitution with the Cholesky factor, by one warp:
+// gather b into canonical order, substitute, scatter back to solve order.
 template <typename V, bool LC = false>
 __device__ void coarse_solve_warp(const CoarseArgs& A, const V* b, V* x) {
   const int lane = threadIdx.x & 31;
@@ -652,22 +653,7 @@ __device__ void coarse_solve_warp(const CoarseArgs& A, const V* b, V* x) {
     A.y[(long long)__ldg(A.perm + r) * d + a] = (double)ldx<LC>(b + t);
   }
   __syncwarp();
-  for (int j = 0; j < n; ++j) {
-    const double ljj = A.chol[(long long)j * n + j];
-    const double yj = A.drop[j] ? 0.0 : A.y[j] / ljj;
-    __syncwarp();
-    if (lane == 0) A.y[j] = yj;
-    for (int i = j + 1 + lane; i < n; i += 32) A.y[i] -= A.chol[(long long)i * n + j] * yj;
-    __syncwarp();
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    const double ljj = A.chol[(long long)j * n + j];
-    const double xj = A.drop[j] ? 0.0 : A.y[j] / ljj;
-    __syncwarp();
-    if (lane == 0) A.y[j] = xj;
-    for (int i = lane; i < j; i += 32) A.y[i] -= A.chol[(long long)j * n + i] * xj;
-    __syncwarp();
-  }
+  chol_substitute_warp(A.chol, A.drop, n, A.y);
   for (int t = lane; t < n; t += 32) {
     const int r = t / d, a = t - r * d;
     stx<LC>(x + t, (V)A.y[(long long)__ldg(A.perm + r) * d + a]);
@@ -2485,6 +2471,62 @@ double time_kernel(Ctx& c, int which, int level, int reps, double* bytes) {
 void lanes_info(Ctx& c, int32_t* g, int n) {
   for (int l = 0; l < n; ++l) g[l] = 0;
   if (c.eng) c.eng->lanes(g, n);
+}
+
+// FP64 FMA throughput: each thread runs FMA_CHAINS independent chains of
+// dependent FMAs (enough independent work to cover the FP64 pipe's latency),
+// `iters` steps each; the result is stored so the chains are not removed.
+constexpr int FMA_CHAINS = 8;
+__global__ void __launch_bounds__(256) fp64_fma_kernel(int iters, double* out) {
+  double a[FMA_CHAINS];
+  const double m = 1.0 - 1e-9 * (double)(threadIdx.x & 7), c = 1e-12 * (double)(blockIdx.x & 15);
+#pragma unroll
+  for (int k = 0; k < FMA_CHAINS; ++k) a[k] = 1.0 + 1e-3 * (double)k + 1e-7 * (double)threadIdx.x;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < FMA_CHAINS; ++k) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < FMA_CHAINS; ++k) s += a[k];
+  if (s == 12345.678) out[0] = s;  // never true; keeps the chains live
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[1] = s;
+}
+
+int probe_fp64_rate(double* tflops, double* ms_out) {
+  cudaStream_t s = nullptr;
+  VASMG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } guard{s};
+  int dev = 0, sms = 0, bpsm = 0;
+  VASMG_CUDA(cudaGetDevice(&dev));
+  VASMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, fp64_fma_kernel, 256, 0));
+  const int blocks = sms * std::max(1, bpsm), iters = 1 << 14;
+  DevBuf<double> out;
+  out.alloc(2, s);
+  fp64_fma_kernel<<<blocks, 256, 0, s>>>(iters, out.get());  // warm-up
+  check_launch("fp64_fma");
+  cudaEvent_t e0, e1;
+  VASMG_CUDA(cudaEventCreate(&e0));
+  VASMG_CUDA(cudaEventCreate(&e1));
+  const int reps = 5;
+  VASMG_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) fp64_fma_kernel<<<blocks, 256, 0, s>>>(iters, out.get());
+  VASMG_CUDA(cudaEventRecord(e1, s));
+  VASMG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.0f;
+  VASMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_launch("fp64_fma");
+  const double per = (double)ms / reps;
+  const double flops = 2.0 * FMA_CHAINS * (double)iters * blocks * 256.0;
+  if (tflops) *tflops = flops / (per * 1e-3) / 1e12;
+  if (ms_out) *ms_out = per;
+  return VASMG_OK;
 }
 
 int probe_wait_timeout(double* elapsed_ms) {

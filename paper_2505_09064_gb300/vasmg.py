@@ -34,9 +34,10 @@ EXPORTED = ["vasmg_default_options", "vasmg_setup", "vasmg_assemble_load", "vasm
             "vasmg_last_launch_count", "vasmg_destroy", "vasmg_error_string", "vasmg_last_error_detail",
             "vasmg_coarse_solve_noalloc", "vasmg_server_default_opts", "vasmg_server_create",
             "vasmg_server_submit", "vasmg_server_poll", "vasmg_server_destroy", "vasmg_update_data",
-            "vasmg_probe_wait_timeout"]
+            "vasmg_probe_wait_timeout", "vasmg_probe_fp64_rate"]
 
 OK, NOT_CONVERGED, PENDING = 0, 1, 2
+NOALLOC_MAX_DOFS = 4096  # VASMG_NOALLOC_MAX_DOFS
 
 
 class vasmg_problem(C.Structure):
@@ -119,6 +120,8 @@ def load():
     lib.vasmg_last_error_detail.restype = C.c_char_p
     lib.vasmg_probe_wait_timeout.argtypes = [C.POINTER(C.c_double)]
     lib.vasmg_probe_wait_timeout.restype = C.c_int
+    lib.vasmg_probe_fp64_rate.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.vasmg_probe_fp64_rate.restype = C.c_int
     _lib = lib
     return lib
 
@@ -234,6 +237,13 @@ def vasmg_probe_wait_timeout():
     return rc, ms.value
 
 
+def vasmg_probe_fp64_rate():
+    """(FP64 TFLOP/s, ms per launch) of an FMA-chain kernel on the current device."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(load().vasmg_probe_fp64_rate(C.byref(tf), C.byref(ms)), "vasmg_probe_fp64_rate")
+    return tf.value, ms.value
+
+
 def vasmg_num_levels(h) -> int:
     n = load().vasmg_num_levels(h)
     if n < 0:
@@ -276,10 +286,24 @@ def vasmg_update_data(h, lam=None, mu=None, lam_const=0.0, mu_const=0.0, dirichl
            "vasmg_update_data")
 
 
-def vasmg_coarse_solve_noalloc(h, b, x, stream=None):
-    """x = A_L^{-1} b on the coarsest level without allocating (b, x: device
-    tensors of dim * coarsest-vertices doubles, canonical order).  Enqueued on
-    `stream` (an int cudaStream_t or None); the caller synchronises."""
+def vasmg_coarse_solve_noalloc(h, b, x, stream=None, n=None):
+    """x = A_L^{-1} b on the coarsest level without allocating (b, x: CUDA
+    float64 tensors of n = dim * coarsest-vertices entries, canonical order, on
+    the current device).  Enqueued on `stream` (an int cudaStream_t or None);
+    the caller synchronises.  n, if given, is checked against both vectors."""
+    import torch
+
+    for a, name in ((b, "b"), (x, "x")):
+        if not (hasattr(a, "data_ptr") and a.is_cuda):
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if a.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on {a.device}, not on the current device")
+        if n is not None:
+            _check_vec(a, n, name)
+        elif a.dtype != torch.float64:
+            raise TypeError(f"{name} must be float64, got {a.dtype}")
+    if b.numel() != x.numel():
+        raise ValueError(f"b has {b.numel()} entries and x {x.numel()}")
     s = C.c_void_p(stream) if isinstance(stream, int) else stream
     _check(load().vasmg_coarse_solve_noalloc(h, _ptr(b), _ptr(x), s), "vasmg_coarse_solve_noalloc")
 
@@ -348,6 +372,12 @@ class Solver:
 
     def apply(self, op, level, x, y):
         vasmg_apply(self.h, op, level, x, y)
+
+    def coarse_solve_noalloc(self, b, x, stream=None):
+        """vasmg_coarse_solve_noalloc with both vectors checked against the
+        coarsest level's dof count."""
+        n = self.level_info(self.num_levels - 1)[0] * self.dim
+        vasmg_coarse_solve_noalloc(self.h, b, x, stream, n=n)
 
     def update(self, prob: dict):
         """Take the material and Dirichlet values of `prob` (same mesh and

@@ -100,3 +100,21 @@ def test_vector_arguments_are_checked_before_the_call():
         vasmg._check_vec(np.zeros(5), 6, "U")
     with pytest.raises(TypeError):
         vasmg._check_vec([0.0] * 6, 6, "U")
+
+
+def test_noalloc_binding_refuses_host_vectors_before_the_call():
+    """vasmg_coarse_solve_noalloc reads its vectors on the device: the binding
+    refuses numpy arrays and CPU tensors before any pointer reaches the
+    library (the handle is never touched, so a dummy one suffices)."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2505_09064_gb300 import vasmg
+
+    dummy = C.c_void_p(1)
+    with pytest.raises(TypeError):
+        vasmg.vasmg_coarse_solve_noalloc(dummy, np.zeros(8), np.zeros(8))
+    with pytest.raises(TypeError):
+        vasmg.vasmg_coarse_solve_noalloc(dummy, torch.zeros(8, dtype=torch.float64),
+                                         torch.zeros(8, dtype=torch.float64))

@@ -25,6 +25,8 @@ def test_reference_arm_prints_one_json_line():
     assert d["value"] > 0
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["cpu_model"] and cb["nproc"] >= 1
+    assert d["config"]["workload"].startswith("cube128_graded")
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

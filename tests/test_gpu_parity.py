@@ -2,10 +2,12 @@
 
 Integer and geometric work must match bit for bit: Morton keys, leaves, cells,
 lattice vertices, interpolation patterns *and weights*, operator patterns,
-dead dofs and colours.  FP64 values match to 1e-12 relative; a full FP64 solve
-matches the oracle's solution to 1e-10 relative with the same iteration count
-(+-1).  Mixed precision solves must reach rel. residual < tol; their error
-against the FP64 oracle is reported.
+dead dofs and colours.  Floating-point results are compared element by
+element: every entry's error relative to the largest entry of the reference
+(max norm).  FP64 values match to 1e-12; a full FP64 solve matches the
+oracle's solution to 1e-10 with the same iteration count (+-1).  Mixed
+precision solves must reach a true relative residual below the tolerance
+(1e-6); their error against the FP64 oracle is reported.
 """
 import numpy as np
 import pytest
@@ -108,7 +110,8 @@ def test_load_vector(built, name):
 
 
 def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    """Element-wise error relative to the reference's largest entry (max norm)."""
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 @pytest.mark.parametrize("name", ["2d_n24", "2d_n37_ragged", "3d_n8", "3d_n11_graded"])
@@ -150,7 +153,7 @@ def test_single_steps(built, name, precision, tol):
         y = torch.zeros(nl, dtype=torch.float64, device="cuda")
         s.apply(vasmg.OP_RESIDUAL, l, dev(b), y)
         ref_r = b - o.apply_A(l, ref_fwd)
-        assert np.linalg.norm(y.cpu().numpy() - ref_r) <= tol * 10 * np.linalg.norm(b)
+        assert np.max(np.abs(y.cpu().numpy() - ref_r)) <= tol * 10 * np.max(np.abs(b))
         # transfers
         nc = o.nv_level(l + 1) * d
         r = rs.uniform(nl, -1, 1)
@@ -204,7 +207,7 @@ def test_mixed_precision_solve(built, name, precision):
     Fr = F.copy()
     Fr[p["dirichlet_dofs"]] = 0.0
     res = np.linalg.norm(Fr - o.apply_A(0, Uh)) / np.linalg.norm(Fr)
-    assert res < 2e-6
+    assert res < 1e-6 * (1 + 1e-6), res
     _, it64, _, _, _ = o.solve(F, tol=1e-6)
     assert st.iterations <= it64 + (3 if precision == "fp32" else 8)
     print(f"{name} {precision}: iters {st.iterations} (fp64 oracle {it64}), "

@@ -5,7 +5,10 @@ depend only on the mesh and on which dofs are constrained, so
 vasmg_update_data recomputes values only.  A handle set up with one material
 and updated to another must then solve exactly like a handle set up with the
 second material from scratch: same iteration count, same solution (bitwise:
-the same kernels run on the same values in the same order).
+the same kernels run on the same values in the same order).  The updated
+handle's FP64 solve is also compared with the CPU oracle set up from scratch
+on the new data (assembly of Sec. 2, Galerkin products eq. (Ac)): iterations
++-1, solution to 1e-10 (max norm).
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from paper_2505_09064_gb300 import meshgen, vasmg  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -79,3 +83,29 @@ def test_update_equals_fresh_setup(built, dim, n, precision, nonhomogeneous):
     finally:
         s.close()
         fresh.close()
+
+
+@pytest.mark.parametrize("dim,n", [(2, 60), (3, 12)])
+@pytest.mark.parametrize("nonhomogeneous", [False, True])
+def test_update_matches_oracle_on_new_data(built, dim, n, nonhomogeneous):
+    p = meshgen.make_problem(None, dim=dim, n=n, jitter=0.2 if dim == 2 else 0.15, seed=80 + n)
+    q = _variant(p, 81 + n, nonhomogeneous)
+    stream = torch.cuda.current_stream().cuda_stream
+    ndof = p["coords"].shape[0] * dim
+    F = meshgen.Stream(82).uniform(ndof, -1.0, 1.0)
+    s = vasmg.Solver(p, precision="fp64", stream=stream)
+    try:
+        _solve(s, F)
+        s.update(q)
+        U1, it1 = _solve(s, F)
+        o = oracle.Oracle(q)
+        U_ref, it_ref, _, st_ref, _ = o.solve(F, tol=1e-8)
+        assert st_ref == 0
+        assert abs(it1 - it_ref) <= 1, (it1, it_ref)
+        err = float(np.max(np.abs(U1 - U_ref)) / np.max(np.abs(U_ref)))
+        assert err <= 1e-10, err
+        if nonhomogeneous:
+            # the new Dirichlet values are written into U
+            assert np.array_equal(U1[q["dirichlet_dofs"]], q["dirichlet_values"])
+    finally:
+        s.close()

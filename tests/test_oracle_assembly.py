@@ -1,7 +1,8 @@
 """Pins for the oracle's P1 elasticity assembly (Sec. 2) against facts that do
 not come from the oracle itself: the textbook Voigt form B^T D B, the paper's
 own 2x2 block form, the rigid-body null space, exact symmetry, the total load,
-and the linear-displacement patch test."""
+the load's distribution over the vertices (one-element closed form and the
+first-moment identity), and the linear-displacement patch test."""
 import numpy as np
 import pytest
 
@@ -89,6 +90,38 @@ def test_total_load_equals_force_times_measure(oracle_mod, dim, n):
     # the mesh covers the unit square / cube exactly
     np.testing.assert_allclose(F.sum(axis=0), f * 1.0, rtol=1e-12)
     np.testing.assert_allclose(o.volumes().sum(), 1.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_single_element_load_closed_form(oracle_mod, dim, seed):
+    """F_i = int_K f phi_i = f |K| / (d+1) for each vertex of one simplex (the
+    integral of a P1 hat function over its element is |K|/(d+1)); |K| from the
+    determinant, computed here."""
+    p = _single_element(dim, seed)
+    o = oracle_mod.Oracle(p, coarse_max_dofs=100)
+    f = meshgen.Stream(40 + seed).uniform(dim, -2.0, 2.0)
+    F = o.assemble_load(f).reshape(dim + 1, dim)
+    X = p["coords"]
+    meas = abs(np.linalg.det((X[1:] - X[0]).T)) / (2.0 if dim == 2 else 6.0)
+    np.testing.assert_allclose(F, np.tile(f * meas / (dim + 1), (dim + 1, 1)), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("dim,n,graded", [(2, 11, None), (2, 9, 8.0), (3, 6, None), (3, 7, 4.0)])
+def test_load_first_moment_identity(oracle_mod, dim, n, graded):
+    """P1 hat functions reproduce linear fields, sum_i phi_i(x) x_i = x, so the
+    consistent load of a constant force satisfies sum_i F_i x_i^T =
+    f int_Omega x^T dx exactly.  On the unit square / cube (which the jittered
+    and graded meshes cover exactly) int x_b dx = 1/2 for every axis b.  A load
+    put on the wrong vertex of an element changes this moment."""
+    p = meshgen.make_problem(None, dim=dim, n=n, jitter=0.0 if graded else (0.2 if dim == 2 else 0.15), seed=8,
+                             graded=graded)
+    o = oracle_mod.Oracle(p)
+    f = np.array([0.7, -1.3, 0.4][:dim])
+    F = o.assemble_load(f).reshape(-1, dim)
+    X = p["coords"]
+    moment = F.T @ X          # [a, b] = sum_i F_{i,a} x_{i,b}
+    np.testing.assert_allclose(moment, np.outer(f, np.full(dim, 0.5)), rtol=1e-12, atol=1e-14)
 
 
 @pytest.mark.parametrize("dim,n", [(2, 10), (3, 6)])

@@ -72,6 +72,12 @@ def parse():
                     help="V-cycle precision (default: the workload's configuration)")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads' lines")
     ap.add_argument("--fp64-peak", action="store_true", help="only measure the FP64 FMA rate and print it")
+    ap.add_argument("--side", type=int, default=0,
+                    help="run the workload's recipe at this many vertices per side (profiling small cases)")
+    ap.add_argument("--profile-kernel", default="",
+                    help="KIND:LEVEL (KIND in spmv64, sweep, fwd_sweep, residual, restrict, prolong, tail): set "
+                         "up the workload, then launch that kernel once between cudaProfilerStart/Stop (for "
+                         "ncu --profile-from-start off) and print its CUDA-event time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="lanes per row by rule (setup then launches no timing runs; for launch-indexed profiles)")
@@ -359,7 +365,7 @@ def ours(args):
         return
 
     def make(workload, precision, threshold=0):
-        prob = meshgen.make_problem(workload)
+        prob = sample_problem(workload, args.side) if args.side else meshgen.make_problem(workload)
         n = prob["coords"].shape[0] * prob["dim"]
         nfree = n - prob["dirichlet_dofs"].size
         s = vasmg.Solver(prob, precision=precision, stream=stream, use_graph=not args.no_graph,
@@ -407,11 +413,34 @@ def ours(args):
         s2.close()
         return out, None
 
+    if args.profile_kernel:
+        kind, level = args.profile_kernel.split(":")
+        which = {"spmv64": vasmg.KERNEL_SPMV64, "sweep": vasmg.KERNEL_SWEEP, "fwd_sweep": vasmg.KERNEL_FWD_SWEEP,
+                 "residual": vasmg.KERNEL_RESIDUAL, "restrict": vasmg.KERNEL_RESTRICT,
+                 "prolong": vasmg.KERNEL_PROLONG, "tail": vasmg.KERNEL_TAIL}[kind]
+        s, F, U, n, nfree = make(args.workload, args.precision)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        kms, kbytes = vasmg.vasmg_time_kernel(s.h, which, int(level), 1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        if rank == 0:
+            print(json.dumps({"profile_kernel": args.profile_kernel, "workload": args.workload, "side": args.side,
+                              "precision": args.precision, "ms": kms, "algorithmic_bytes": kbytes,
+                              "lanes_per_row": [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)],
+                              "level_vertices": [vasmg.vasmg_level_info(s.h, l)[0]
+                                                 for l in range(vasmg.vasmg_num_levels(s.h))]}), flush=True)
+        s.close()
+        return
     # headline
     s, F, U, n, nfree = make(args.workload, args.precision)
     clocks = ClockSampler(local)
     clocks.start()
+    if args.solve_only:
+        torch.cuda.profiler.start()  # the solves alone, for ncu --profile-from-start off
     ms, iters, launches, st = timed(s, F, U, args.steps)
+    if args.solve_only:
+        torch.cuda.profiler.stop()
     clk = clocks.stop()
     ms, work = reduce_over_ranks(ms, float(nfree * sum(iters)), dev)
     value = work / (ms / 1e3) / 1e6
@@ -421,6 +450,7 @@ def ours(args):
                               "unit": "MDOF*iter/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                               "ms_per_step": ms / args.steps, "iterations": iters[0], "gpu_launches": launches,
                               "graph": not args.no_graph, "solve_only": True, "workload": args.workload,
+                              "side": args.side,
                               "precision": args.precision, "clocks": clk,
                               "lanes_per_row": [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)]}),
                   flush=True)

@@ -9,7 +9,10 @@ array instead of allocating per call.
 
 Checked here, on two calls in a row and in place:
   - it equals vasmg_apply(VASMG_OP_COARSE) (the allocating path, same FP64
-    substitution) to 1e-13 relative, max norm;
+    substitution) to 1e-13 relative, max norm, on FP64 handles; on FP32 and
+    BF16-smoother handles vasmg_apply stages its vectors in the V-cycle's
+    FP32 precision while this entry point stays in FP64, so there the two
+    agree to FP32 rounding (1e-5);
   - it equals the CPU oracle's coarsest solve (its own Cholesky factor) to
     1e-10 relative, max norm;
   - for FP64, FP32 and BF16-smoother handles (every mode keeps the FP64
@@ -82,16 +85,17 @@ def test_noalloc_coarse_solve_matches_apply_and_oracle(built, name, precision):
             s.coarse_solve_noalloc(b, x, stream)
             torch.cuda.synchronize()
             outs.append(x.cpu().numpy())
+        tol_apply = 1e-13 if precision == "fp64" else 1e-5
         for x in outs:
             assert np.all(np.isfinite(x))
-            assert _rel(x, ref_h) <= 1e-13
+            assert _rel(x, ref_h) <= tol_apply
             assert _rel(x, x_or) <= 1e-10
         assert np.array_equal(outs[0], outs[1])
         # in place (b and x the same buffer)
         y = b.clone()
         s.coarse_solve_noalloc(y, y, stream)
         torch.cuda.synchronize()
-        assert _rel(y.cpu().numpy(), ref_h) <= 1e-13
+        assert np.array_equal(y.cpu().numpy(), outs[0])
     finally:
         s.close()
 

@@ -160,6 +160,25 @@ int vasmg_assemble_load(vasmg_handle h, const double* body_force, double* F);
  * NULL.  Returns VASMG_OK, VASMG_NOT_CONVERGED or an error. */
 int vasmg_solve(vasmg_handle h, const double* F, double* U, double tol, vasmg_stats* st);
 
+/* k right-hand sides on one hierarchy: k independent PCG solves (Alg. 2 with
+ * the V-cycle of Alg. 3) of A U_i = F_i, each to tol, advanced together.  In
+ * the FP32-vector modes every kernel of an iteration reads the operators once
+ * for up to 8 right-hand sides (the sweeps, residuals and transfers apply each
+ * block or weight to all of them; the FP64 SpMV to 4 at a time), so the
+ * iterations cost less than k separate ones.  Each right-hand side follows
+ * exactly the arithmetic of vasmg_solve: U_i, its iteration count and its
+ * residual history are bitwise those of vasmg_solve(h, F[i], U[i], tol, ...);
+ * a right-hand side that has converged keeps its iterate while the others go
+ * on.  The paper solves one right-hand side at a time; this is the same solve
+ * batched.
+ *   F, U  arrays of k pointers to [n] doubles (host or device)
+ *   st    NULL or an array of k stats (solve_ms is the whole call's)
+ * With VASMG_FP64 the k solves run one after another.  The first call with a
+ * given number of right-hand sides (rounded up to 2, 4 or 8 per pass) builds
+ * that pass's vectors and graph.  Returns the most severe status. */
+int vasmg_solve_multi(vasmg_handle h, int32_t k, const double* const* F, double* const* U, double tol,
+                      vasmg_stats* st);
+
 /* Solve k independent systems (uneven sizes allowed), each to tol, sharing
  * the device; h[i] may repeat.  st may be NULL or an array of k stats.
  *
@@ -349,6 +368,14 @@ enum {
                                     single cluster launch that runs the small levels */
 };
 int vasmg_time_kernel(vasmg_handle h, int32_t which, int32_t level, int32_t reps, double* ms, double* bytes);
+
+/* As vasmg_time_kernel for the kernels of vasmg_solve_multi with k = 2, 4 or
+ * 8 right-hand sides per launch (VASMG_KERNEL_SPMV64, _SWEEP, _VCYCLE,
+ * _FWD_SWEEP, _RESIDUAL, _RESTRICT, _PROLONG, _TAIL; FP32-vector modes only,
+ * else VASMG_ERR_UNSUPPORTED).  *bytes counts the operator arrays once and
+ * every vector entry once per right-hand side (0 for the tail). */
+int vasmg_time_kernel_multi(vasmg_handle h, int32_t which, int32_t level, int32_t k, int32_t reps, double* ms,
+                            double* bytes);
 
 /* Measured FP64 FMA throughput of the current device, the arithmetic roof of
  * the FP64 kernels (the outer CG's SpMV): a kernel of independent FMA chains

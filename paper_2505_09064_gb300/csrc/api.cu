@@ -300,6 +300,31 @@ int vasmg_solve(vasmg_handle h, const double* F, double* U, double tol, vasmg_st
   VASMG_API_END
 }
 
+int vasmg_solve_multi(vasmg_handle h, int32_t k, const double* const* F, double* const* U, double tol,
+                      vasmg_stats* st) {
+  if (!h || k < 0 || !(tol > 0.0) || (k > 0 && (!F || !U))) return VASMG_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < k; ++i)
+    if (!F[i] || !U[i]) return VASMG_ERR_INVALID_ARG;
+  if (k == 0) return VASMG_OK;
+  VASMG_API_BEGIN
+  Ctx& c = h->c;
+  const double t0 = now_ms();
+  join_user(c);
+  const int rc = solve_multi_dev(c, k, F, U, tol, st);
+  if (st) {
+    const double ms = now_ms() - t0;
+    double nb0 = (double)c.C[0].nnzb, tot = 0;
+    for (auto& l : c.C) tot += (double)l.nnzb;
+    for (int32_t i = 0; i < k; ++i) {
+      st[i].solve_ms = ms;
+      st[i].setup_ms = c.setup_ms;
+      st[i].op_complexity = tot / nb0;
+    }
+  }
+  return rc;
+  VASMG_API_END
+}
+
 int vasmg_solve_batch(int32_t k, const vasmg_handle* h, const double* const* F, double* const* U, double tol,
                       vasmg_stats* st) {
   if (k < 0 || (k > 0 && (!h || !F || !U))) return VASMG_ERR_INVALID_ARG;
@@ -506,6 +531,17 @@ int vasmg_time_kernel(vasmg_handle h, int32_t which, int32_t level, int32_t reps
   VASMG_API_BEGIN
   join_user(h->c);
   *ms = time_kernel(h->c, which, level, reps, bytes);
+  return VASMG_OK;
+  VASMG_API_END
+}
+
+int vasmg_time_kernel_multi(vasmg_handle h, int32_t which, int32_t level, int32_t k, int32_t reps, double* ms,
+                            double* bytes) {
+  if (!h || !ms || !bytes || reps <= 0 || (k != 2 && k != 4 && k != 8)) return VASMG_ERR_INVALID_ARG;
+  if (level < 0 || level >= (int32_t)h->c.C.size()) return VASMG_ERR_INVALID_ARG;
+  VASMG_API_BEGIN
+  join_user(h->c);
+  *ms = time_kernel_multi(h->c, which, level, k, reps, bytes);
   return VASMG_OK;
   VASMG_API_END
 }

@@ -206,6 +206,9 @@ struct EngineBase {
   virtual void dense_level(int* k, int* n) const = 0;
   // lanes per row of the region levels (levels below the tail), 0 elsewhere
   virtual void lanes(int32_t* g, int n) const = 0;
+  // k right-hand sides on this hierarchy (solve_multi.cu for the FP32-vector modes)
+  virtual int solve_multi(Ctx& c, int k, const double* const* F, double* const* U, double tol, vasmg_stats* st) = 0;
+  virtual double time_multi(Ctx& c, int which, int level, int k, int reps, double* bytes) = 0;
 };
 
 // Lanes per row measured rather than picked by rule (vasmg_options.autotune):
@@ -274,9 +277,11 @@ struct Engine : EngineBase {
   cudaGraphExec_t exec_body = nullptr;
   i64 launches_body = 0;
   i64 launch_counter = 0;
+  MultiBase* multi = nullptr;  // several right-hand sides (FP32-vector modes), made on first use
 
   explicit Engine(Ctx& ctx) : c(&ctx) { build(); }
   ~Engine() override {
+    delete multi;
     if (exec_while) cudaGraphExecDestroy(exec_while);
     if (exec_body) cudaGraphExecDestroy(exec_body);
     if (host_sc) cudaFreeHost(host_sc);
@@ -1060,6 +1065,76 @@ struct Engine : EngineBase {
     return host_sc->status;
   }
 
+  // ---------------------------------------------------------------- several right-hand sides
+  EngineView<V> view() {
+    EngineView<V> v;
+    v.stream = c->stream;
+    v.L = L;
+    v.lt = lt;
+    v.nct = nct;
+    v.sms = sms_;
+    v.max_iters = c->max_iters;
+    v.use_graph = c->use_graph;
+    v.lv = lv;
+    v.G = G;
+    for (int l = 0; l < L; ++l) {
+      v.nv.push_back(c->S[l].nv);
+      v.pnnz.push_back(l + 1 < L ? (double)c->C[l].pnnz : 0.0);
+    }
+    v.tail_smem = fill_tail_args(v.ta, lt, one_cta_start(lt));
+    if (kd >= 0 && kd >= v.ta.ls) {
+      v.ta.kd = kd;
+      v.ta.dn = dn;
+      v.ta.dld = dld;
+      v.ta.dm = dm.get();
+      v.ta.dsoff = (int)(v.tail_smem / sizeof(V));
+    }
+    v.cga = cga;
+    v.cga.cond = 0;
+    v.cg_blocks = cg_blocks;
+    v.spmv_blocks = spmv_blocks;
+    v.sell_real_entries = sell_real_entries;
+    v.ctr = ctrs.get();
+    return v;
+  }
+  MultiBase* get_multi() {
+    if constexpr (std::is_same<V, float>::value) {
+      if (!multi) multi = make_multi<D, S>(view());
+      else multi->set_view(view());
+      return multi;
+    }
+    return nullptr;
+  }
+  int solve_multi(Ctx& ctx, int k, const double* const* F, double* const* Uo, double tol, vasmg_stats* st) override {
+    if (k == 1) return solve(ctx, F[0], Uo[0], tol, st);
+    if constexpr (std::is_same<V, float>::value) {
+      i64 launches = 0;
+      const int rc = get_multi()->solve(k, F, Uo, tol, st, &launches);
+      ctx.last_launches = launches;
+      return rc;
+    } else {
+      // the FP64 V-cycle: one solve after another
+      int worst = VASMG_OK;
+      i64 launches = 0;
+      for (int i = 0; i < k; ++i) {
+        const int rc = solve(ctx, F[i], Uo[i], tol, st ? st + i : nullptr);
+        launches += ctx.last_launches;
+        if (rc < 0) worst = std::min(worst, rc);
+        else if (worst >= 0) worst = std::max(worst, rc);
+      }
+      ctx.last_launches = launches;
+      return worst;
+    }
+  }
+  double time_multi(Ctx& ctx, int which, int level, int k, int reps, double* bytes) override {
+    (void)ctx;
+    if constexpr (std::is_same<V, float>::value) {
+      return get_multi()->time(which, level, k, reps, bytes);
+    } else {
+      throw Error(VASMG_ERR_UNSUPPORTED, "several right-hand sides per launch need an FP32-vector V-cycle");
+    }
+  }
+
   // ---------------------------------------------------------------- single steps
   void to_solve(const double* x, V* out, int l, cudaStream_t s) {
     to_solve_kernel<V><<<grid_for((i64)lv[l].nv * D, 256), 256, 0, s>>>(x, out, c->S[l].perm.get(), lv[l].nv, D);
@@ -1298,6 +1373,14 @@ void apply_op(Ctx& c, int op, int level, const double* x_dev, double* y_dev) {
 
 double time_kernel(Ctx& c, int which, int level, int reps, double* bytes) {
   return c.eng->time(c, which, level, reps, bytes);
+}
+
+int solve_multi_dev(Ctx& c, int k, const double* const* F, double* const* U, double tol, vasmg_stats* st) {
+  return c.eng->solve_multi(c, k, F, U, tol, st);
+}
+
+double time_kernel_multi(Ctx& c, int which, int level, int k, int reps, double* bytes) {
+  return c.eng->time_multi(c, which, level, k, reps, bytes);
 }
 
 void lanes_info(Ctx& c, int32_t* g, int n) {

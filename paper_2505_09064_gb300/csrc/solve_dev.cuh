@@ -1166,4 +1166,41 @@ __global__ void cg_final_kernel(CGArgs a, double* __restrict__ Uout) {
 }
 
 
+// ------------------------------------------------------------------ several right-hand sides (solve_multi.cu)
+
+// What the engine of one hierarchy hands to its solver for several
+// right-hand sides: the level views (operators, transfers, region tables and
+// progress words, with the single-vector x, b, r), the lanes per row of the
+// region levels, the tail launch's arguments, and the outer CG's layout.  The
+// device arrays stay owned by the engine; the view is taken again before
+// every call, so new values (vasmg_update_data) are seen.
+template <typename V>
+struct EngineView {
+  cudaStream_t stream = 0;
+  int L = 0, lt = 0, nct = 1, sms = 1, max_iters = 1000, use_graph = 1;
+  std::vector<LV<V>> lv;
+  std::vector<int> G;              // lanes per row of the region levels (l < lt)
+  std::vector<i64> nv;             // vertices per level
+  std::vector<double> pnnz;        // transfer entries of level l -> l+1
+  TailArgs<V> ta;                  // the tail launch from level lt (dense level fields set if used)
+  size_t tail_smem = 0;            // its dynamic shared memory, without the staging of b_kd
+  CGArgs cga;                      // level-0 FP64 operator (SELL), permutation, Dirichlet data
+  int cg_blocks = 1, spmv_blocks = 1;
+  i64 sell_real_entries = 0;
+  int* ctr = nullptr;              // per-level launch counters (epochs), shared with the single path
+};
+
+// k independent PCG solves on one hierarchy whose every sweep, transfer and
+// SpMV reads the operators once for all k (solve_multi.cu).
+struct MultiBase {
+  virtual ~MultiBase() {}
+  virtual void set_view(const EngineView<float>& v) = 0;
+  virtual int solve(int k, const double* const* F, double* const* U, double tol, vasmg_stats* st,
+                    i64* launches) = 0;
+  virtual double time(int which, int level, int k, int reps, double* bytes) = 0;
+};
+template <int D, typename S>
+MultiBase* make_multi(const EngineView<float>& v);
+
+
 }  // namespace vasmg

@@ -34,7 +34,7 @@ EXPORTED = ["vasmg_default_options", "vasmg_setup", "vasmg_assemble_load", "vasm
             "vasmg_last_launch_count", "vasmg_destroy", "vasmg_error_string", "vasmg_last_error_detail",
             "vasmg_coarse_solve_noalloc", "vasmg_server_default_opts", "vasmg_server_create",
             "vasmg_server_submit", "vasmg_server_poll", "vasmg_server_destroy", "vasmg_update_data",
-            "vasmg_probe_wait_timeout", "vasmg_probe_fp64_rate"]
+            "vasmg_probe_wait_timeout", "vasmg_probe_fp64_rate", "vasmg_solve_multi", "vasmg_time_kernel_multi"]
 
 OK, NOT_CONVERGED, PENDING = 0, 1, 2
 NOALLOC_MAX_DOFS = 4096  # VASMG_NOALLOC_MAX_DOFS
@@ -97,6 +97,9 @@ def load():
     lib.vasmg_assemble_load.argtypes = [P, P, P]
     lib.vasmg_solve.argtypes = [P, P, P, C.c_double, C.POINTER(vasmg_stats)]
     lib.vasmg_solve_batch.argtypes = [C.c_int32, P, P, P, C.c_double, P]
+    lib.vasmg_solve_multi.argtypes = [P, C.c_int32, P, P, C.c_double, P]
+    lib.vasmg_time_kernel_multi.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]
     lib.vasmg_num_levels.argtypes = [P]
     lib.vasmg_level_info.argtypes = [P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_int32)]
@@ -227,6 +230,30 @@ def vasmg_solve_batch(handles, Fs, Us, tol: float = 1e-6):
     rc = _check(load().vasmg_solve_batch(k, H, Fp, Up, float(tol), st), "vasmg_solve_batch",
                 allow_not_converged=True)
     return rc, list(st)
+
+
+def vasmg_solve_multi(h, Fs, Us, tol: float = 1e-6, history_cap: int = 0):
+    """k right-hand sides on one hierarchy.  Returns (status, [vasmg_stats],
+    [history ndarray])."""
+    k = len(Fs)
+    Fp = (C.c_void_p * k)(*[_ptr(F).value for F in Fs])
+    Up = (C.c_void_p * k)(*[_ptr(U).value for U in Us])
+    st = (vasmg_stats * k)()
+    hists = [np.zeros(max(1, history_cap)) for _ in range(k)]
+    if history_cap:
+        for i in range(k):
+            st[i].res_history = hists[i].ctypes.data_as(C.c_void_p)
+            st[i].res_history_cap = history_cap
+    rc = _check(load().vasmg_solve_multi(h, k, Fp, Up, float(tol), st), "vasmg_solve_multi",
+                allow_not_converged=True)
+    return rc, list(st), [hists[i][: min(st[i].iterations, history_cap)] for i in range(k)]
+
+
+def vasmg_time_kernel_multi(h, which: int, level: int, k: int, reps: int = 10):
+    ms, nbytes = C.c_double(), C.c_double()
+    _check(load().vasmg_time_kernel_multi(h, which, level, k, reps, C.byref(ms), C.byref(nbytes)),
+           "vasmg_time_kernel_multi")
+    return ms.value, nbytes.value
 
 
 def vasmg_probe_wait_timeout():
@@ -372,6 +399,14 @@ class Solver:
 
     def apply(self, op, level, x, y):
         vasmg_apply(self.h, op, level, x, y)
+
+    def solve_multi(self, Fs, Us, tol=1e-6, history_cap=0):
+        if len(Fs) != len(Us):
+            raise ValueError(f"{len(Fs)} right-hand sides and {len(Us)} solutions")
+        for i, (F, U) in enumerate(zip(Fs, Us)):
+            _check_vec(F, self.n, f"F[{i}]")
+            _check_vec(U, self.n, f"U[{i}]")
+        return vasmg_solve_multi(self.h, Fs, Us, tol, history_cap)
 
     def coarse_solve_noalloc(self, b, x, stream=None):
         """vasmg_coarse_solve_noalloc with both vectors checked against the

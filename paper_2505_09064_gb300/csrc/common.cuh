@@ -320,9 +320,14 @@ __host__ __device__ inline u64 splitmix64(u64 x) {
 
 // Storage of component q (row-major in the d x d block) of block k among n
 // blocks: 2 x 2 blocks are stored contiguously (one 8- or 16-byte load per
-// block), 3 x 3 blocks as d*d planes of n values (coalesced across rows).
+// block); of a 3 x 3 block the first 8 components are stored contiguously
+// (one 16-byte load in BF16, two in FP32, four in FP64) and the ninth in a
+// plane of n values after them, so a block costs 2, 3 or 5 loads instead of
+// 9 and no padding.
 __host__ __device__ inline long long block_index(int q, long long k, long long n, int dd) {
-  return dd == 4 ? k * 4 + q : (long long)q * n + k;
+  if (dd == 4) return k * 4 + q;
+  if (dd == 9) return q < 8 ? k * 8 + q : 8 * n + k;
+  return (long long)q * n + k;
 }
 
 // Forward and backward substitution with a dense lower Cholesky factor L

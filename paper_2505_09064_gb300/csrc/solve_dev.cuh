@@ -74,6 +74,32 @@ __device__ __forceinline__ void ldv4(const S* p, V (&a)[4]) {
   }
 }
 
+// Components 0..7 of a 3 x 3 block, stored contiguously: one 16-byte load
+// for BF16, two for FP32, four for FP64.
+template <typename V, typename S, int N>
+__device__ __forceinline__ void ldv8(const S* p, V (&a)[N]) {
+  static_assert(N >= 8, "a 3 x 3 block");
+  if constexpr (std::is_same<S, float>::value) {
+    const float4 t0 = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 t1 = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    a[0] = t0.x, a[1] = t0.y, a[2] = t0.z, a[3] = t0.w, a[4] = t1.x, a[5] = t1.y, a[6] = t1.z, a[7] = t1.w;
+  } else if constexpr (std::is_same<S, double>::value) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const double2 t = __ldg(reinterpret_cast<const double2*>(p) + h);
+      a[2 * h] = t.x, a[2 * h + 1] = t.y;
+    }
+  } else {
+    const uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const __nv_bfloat162 v2 = *reinterpret_cast<const __nv_bfloat162*>(&w[h]);
+      a[2 * h] = __low2float(v2), a[2 * h + 1] = __high2float(v2);
+    }
+  }
+}
+
 // vectors written inside a launch by other CTAs are read from L2 (.cg)
 // LC: the vector is produced and consumed by one CTA only, so plain (L1-cached)
 // accesses are coherent after a CTA barrier.
@@ -87,18 +113,31 @@ __device__ __forceinline__ void stx(V* p, V v) {
   if constexpr (LC) *p = v;
   else __stcg(p, v);
 }
+// A vector value written inside the launch by other CTAs: from L2 (.cg), or
+// (L1) through the SM's L1 cache.  L1 is used only by the region launches,
+// whose every colour step starts after a GPU-scope acquire (the neighbour
+// wait), which invalidates the SM's L1: a cached value is then never older
+// than the last step's, and within a step no value a row reads is written
+// (rows of one colour are not neighbours).  Rows of a region share most of
+// their neighbours, so their gathers mostly hit L1.
+template <bool L1, typename T>
+__device__ __forceinline__ T ld_shared_vec(const T* p) {
+  if constexpr (L1) return __ldca(p);
+  else return __ldcg(p);
+}
+
 // The D components of one vertex from global memory: one 8- or 16-byte load
 // for D = 2 (rows of 2 values are aligned to their size), a pair and a
 // single for D = 3 unless PAIR3 is false (the region sweeps: measured slower
 // there); one load per component from shared memory.
-template <int D, bool LC = false, bool PAIR3 = true, typename V>
+template <int D, bool LC = false, bool PAIR3 = true, bool L1 = false, typename V>
 __device__ __forceinline__ void ldx_vertex(const V* p, V (&v)[D]) {
   if constexpr (D == 2 && !LC && std::is_same<V, float>::value) {
-    const float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+    const float2 t = ld_shared_vec<L1>(reinterpret_cast<const float2*>(p));
     v[0] = t.x;
     v[1] = t.y;
   } else if constexpr (D == 2 && !LC && std::is_same<V, double>::value) {
-    const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+    const double2 t = ld_shared_vec<L1>(reinterpret_cast<const double2*>(p));
     v[0] = t.x;
     v[1] = t.y;
   } else if constexpr (D == 3 && !LC && PAIR3 && (std::is_same<V, float>::value || std::is_same<V, double>::value)) {
@@ -107,16 +146,19 @@ __device__ __forceinline__ void ldx_vertex(const V* p, V (&v)[D]) {
     // which pair is aligned)
     using V2 = typename std::conditional<std::is_same<V, float>::value, float2, double2>::type;
     if (((reinterpret_cast<uintptr_t>(p) / sizeof(V)) & 1) == 0) {
-      const V2 t = __ldcg(reinterpret_cast<const V2*>(p));
+      const V2 t = ld_shared_vec<L1>(reinterpret_cast<const V2*>(p));
       v[0] = t.x;
       v[1] = t.y;
-      v[2] = __ldcg(p + 2);
+      v[2] = ld_shared_vec<L1>(p + 2);
     } else {
-      v[0] = __ldcg(p);
-      const V2 t = __ldcg(reinterpret_cast<const V2*>(p + 1));
+      v[0] = ld_shared_vec<L1>(p);
+      const V2 t = ld_shared_vec<L1>(reinterpret_cast<const V2*>(p + 1));
       v[1] = t.x;
       v[2] = t.y;
     }
+  } else if constexpr (!LC) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = ld_shared_vec<L1>(p + a);
   } else {
 #pragma unroll
     for (int a = 0; a < D; ++a) v[a] = ldx<LC>(p + a);
@@ -245,11 +287,22 @@ __device__ __forceinline__ int seg_entry(const RowSeg& r, int e, const int* ciA,
     (void)n;
     ldv4<V, S>(op + (long long)k * 4, a);  // 2D blocks are stored contiguously
   } else {
-#pragma unroll
-    for (int q = 0; q < D * D; ++q) a[q] = ldv<V, S>(op + (long long)q * n + k);
+    ldv8<V, S>(op + (long long)k * 8, a);  // components 0..7 contiguous (block_index)
+    a[8] = ldv<V, S>(op + 8 * n + k);
   }
   return __ldg(cp + k);
 }
+
+// Gathers of a region level go through L1 (see ld_shared_vec); the cluster
+// tail's levels keep L2 loads.
+template <typename V>
+struct TL;
+template <typename L_t>
+struct is_tail_level : std::false_type {};
+template <typename V>
+struct is_tail_level<TL<V>> : std::true_type {};
+template <typename L_t, bool LC>
+constexpr bool gather_l1() { return !LC && !is_tail_level<L_t>::value; }
 
 // acc += sum over the row entries e = e0, e0 + G, ... < len of A_e x_{col(e)},
 // one entry at a time.  PAIR3: 3D vertex values gathered as an aligned pair
@@ -269,7 +322,7 @@ __device__ __forceinline__ void row_entries(const L_t& L, const RowSeg& sg, int 
     V blk[D * D];
     const int j = seg_entry<D, V, S>(sg, e, ciA, offA, nA, ciB, offB, nB, blk);
     V xj[D];
-    ldx_vertex<D, LC, PAIR3>((const V*)L.x + (long long)j * D, xj);
+    ldx_vertex<D, LC, PAIR3, gather_l1<L_t, LC>()>((const V*)L.x + (long long)j * D, xj);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -354,7 +407,7 @@ __device__ __forceinline__ void row_finish(const L_t& L, int row, bool valid, in
   for (int p = 0; p < NPF; ++p) {
     if (st.cj[p] >= 0) {
       V xj[D];
-      ldx_vertex<D, LC, false>((const V*)L.x + (long long)st.cj[p] * D, xj);
+      ldx_vertex<D, LC, false, gather_l1<L_t, LC>()>((const V*)L.x + (long long)st.cj[p] * D, xj);
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -386,7 +439,7 @@ __device__ __forceinline__ void restrict_row(const L_t& L, int I) {
     const int i = __ldg(L.rci + t);
     const V w = __ldg((const V*)L.rw + t);
     V ri[D];
-    ldx_vertex<D, LC>((const V*)L.r + (long long)i * D, ri);
+    ldx_vertex<D, LC, true, gather_l1<L_t, LC>()>((const V*)L.r + (long long)i * D, ri);
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] += w * ri[a];
   }
@@ -403,7 +456,7 @@ __device__ __forceinline__ void prolong_row(const L_t& L, int i) {
     const int J = __ldg(L.pci + t);
     const V w = __ldg((const V*)L.pw + t);
     V xJ[D];
-    ldx_vertex<D, LC>((const V*)L.xc + (long long)J * D, xJ);
+    ldx_vertex<D, LC, true, gather_l1<L_t, LC>()>((const V*)L.xc + (long long)J * D, xJ);
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] += w * xJ[a];
   }

@@ -30,26 +30,27 @@ constexpr int TAILM_THREADS = 512;  // threads of the multi tail CTAs (more regi
 constexpr int KMAX = 8;             // right-hand sides per pass
 constexpr int KG_SPMV = 4;          // right-hand sides per SpMV launch
 
-// N consecutive vector values (a vertex's KR x D entries) from L2: 16-byte
+// N consecutive vector values (a vertex's KR x D entries), through L1 on the
+// region levels and from L2 on the tail's levels (see ld_shared_vec): 16-byte
 // loads when N is a multiple of 4 (the block starts on a 16-byte boundary),
 // else 8-byte loads.
-template <int N>
-__device__ __forceinline__ void ld_cg_n(const float* p, float (&v)[N]) {
+template <int N, bool L1>
+__device__ __forceinline__ void ld_vec_n(const float* p, float (&v)[N]) {
   if constexpr (N % 4 == 0) {
 #pragma unroll
     for (int q = 0; q < N / 4; ++q) {
-      const float4 t = __ldcg(reinterpret_cast<const float4*>(p) + q);
+      const float4 t = ld_shared_vec<L1>(reinterpret_cast<const float4*>(p) + q);
       v[4 * q] = t.x, v[4 * q + 1] = t.y, v[4 * q + 2] = t.z, v[4 * q + 3] = t.w;
     }
   } else if constexpr (N % 2 == 0) {
 #pragma unroll
     for (int q = 0; q < N / 2; ++q) {
-      const float2 t = __ldcg(reinterpret_cast<const float2*>(p) + q);
+      const float2 t = ld_shared_vec<L1>(reinterpret_cast<const float2*>(p) + q);
       v[2 * q] = t.x, v[2 * q + 1] = t.y;
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < N; ++q) v[q] = __ldcg(p + q);
+    for (int q = 0; q < N; ++q) v[q] = ld_shared_vec<L1>(p + q);
   }
 }
 
@@ -102,7 +103,7 @@ __device__ __forceinline__ void rowm_finish(const L_t& L, int row, bool valid, i
     for (int a = 0; a < D; ++a) acc[i][a] = V(0);
   if (st.cj >= 0) {
     V xj[KR * D];
-    ld_cg_n<KR * D>((const V*)L.x + (long long)st.cj * KR * D, xj);
+    ld_vec_n<KR * D, gather_l1<L_t, false>()>((const V*)L.x + (long long)st.cj * KR * D, xj);
 #pragma unroll
     for (int i = 0; i < KR; ++i)
 #pragma unroll
@@ -121,7 +122,7 @@ __device__ __forceinline__ void rowm_finish(const L_t& L, int row, bool valid, i
     V blk[D * D];
     const int j = seg_entry<D, V, S>(st.sg, e, ciA, offA, nA, ciB, offB, nB, blk);
     V xj[KR * D];
-    ld_cg_n<KR * D>((const V*)L.x + (long long)j * KR * D, xj);
+    ld_vec_n<KR * D, gather_l1<L_t, false>()>((const V*)L.x + (long long)j * KR * D, xj);
 #pragma unroll
     for (int i = 0; i < KR; ++i)
 #pragma unroll
@@ -175,7 +176,7 @@ __device__ __forceinline__ void restrictm_row(const L_t& L, int I) {
     const int i = __ldg(L.rci + t);
     const V w = __ldg((const V*)L.rw + t);
     V ri[KR * D];
-    ld_cg_n<KR * D>((const V*)L.r + (long long)i * KR * D, ri);
+    ld_vec_n<KR * D, gather_l1<L_t, false>()>((const V*)L.r + (long long)i * KR * D, ri);
 #pragma unroll
     for (int q = 0; q < KR * D; ++q) acc[q] += w * ri[q];
   }
@@ -193,7 +194,7 @@ __device__ __forceinline__ void prolongm_row(const L_t& L, int i) {
     const int J = __ldg(L.pci + t);
     const V w = __ldg((const V*)L.pw + t);
     V xJ[KR * D];
-    ld_cg_n<KR * D>((const V*)L.xc + (long long)J * KR * D, xJ);
+    ld_vec_n<KR * D, gather_l1<L_t, false>()>((const V*)L.xc + (long long)J * KR * D, xJ);
 #pragma unroll
     for (int q = 0; q < KR * D; ++q) acc[q] += w * xJ[q];
   }

@@ -44,13 +44,11 @@ TAIL_NV = 20000         # levels this small run inside the single cluster tail l
 # solve takes about 10 s on one core)
 SAMPLE_N = {"cube128_graded": 32, "cube64": 32, "square1024_checker": 192, "square64": 64}
 # DRAM bytes (read + write) of one launch from an ncu capture of the current
-# kernel (profiles/); absent when the kernel changed after the capture
+# kernel (profiles/); absent when the kernel changed after the capture.  The
+# 128^3 entry is a capture of the same recipe at 64^3 (323.8 MB against
+# 322.1 MB algorithmic) scaled by the algorithmic bytes of the full launch.
 TRAFFIC = {
-    ("square1024_checker", "bwd_sweep_l1"): 235454464.0,
-    ("square1024_checker", "fwd_sweep_l1"): 124237312.0,
-    ("square1024_checker", "residual_l0"): 75727104.0,
-    ("square1024_checker", "tail_l4"): 29554688.0,
-    ("square1024_checker", "spmv64_sell"): 314983424.0,
+    ("cube128_graded", "bwd_sweep_l1"): 2303611630.0,
 }
 TOL = 1e-6
 
@@ -346,6 +344,68 @@ def spmv64_flops(s, vasmg):
     return 2.0 * d * d * nnzb + 2.0 * nv * d
 
 
+def multi_rhs_run(s, F, n, nfree, k, dev, peaks):
+    """k right-hand sides on the headline hierarchy: the first is the
+    workload's load, the others body-force loads in seeded random directions.
+    Times one vasmg_solve_multi call against the k single solves (CUDA
+    events), checks that every solution is bitwise the single one, and times
+    the region kernels with k right-hand sides per launch."""
+    import torch
+
+    from paper_2505_09064_gb300 import meshgen, vasmg
+
+    rs = meshgen.Stream(123)
+    d = s.dim
+    Fs = [F]
+    for i in range(1, k):
+        Fi = torch.zeros(n, dtype=torch.float64, device=dev)
+        s.assemble_load(rs.uniform(d, -1.0, 1.0), Fi)
+        Fs.append(Fi)
+    Us = [torch.zeros_like(Fi) for Fi in Fs]
+    s.solve_multi(Fs, Us, TOL)  # warm-up: buffers and graph of the pass
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    rc, sts, _ = s.solve_multi(Fs, Us, TOL)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_multi = ev0.elapsed_time(ev1)
+    launches_multi = vasmg.vasmg_last_launch_count(s.h)
+    its = [st.iterations for st in sts]
+    U1 = torch.zeros_like(F)
+    ev0.record()
+    single_its, bitwise = [], True
+    for i in range(k):
+        rc1, st1, _ = s.solve(Fs[i], U1, TOL)
+        single_its.append(st1.iterations)
+        bitwise = bitwise and bool(torch.equal(U1, Us[i]))
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_single = ev0.elapsed_time(ev1)
+    work = float(nfree * sum(its))
+    out = {"k": k, "value": work / (ms_multi / 1e3) / 1e6, "unit": "MDOF*iter/s", "ms": ms_multi,
+           "solves_per_s": k / (ms_multi / 1e3), "iterations": its, "gpu_launches": launches_multi,
+           "single_solves": {"value": work / (ms_single / 1e3) / 1e6, "ms": ms_single, "iterations": single_its},
+           "speedup_vs_single": ms_single / ms_multi, "bitwise_equal_to_single": bitwise and its == single_its}
+    # the region kernels with k right-hand sides per launch: operator bytes
+    # once, vector bytes k times
+    kern = {}
+    nlev = vasmg.vasmg_num_levels(s.h)
+    for l in range(nlev - 1):
+        if vasmg.vasmg_level_info(s.h, l)[0] <= TAIL_NV:
+            break
+        for name, which in (("fwd_sweep", vasmg.KERNEL_FWD_SWEEP), ("residual", vasmg.KERNEL_RESIDUAL),
+                            ("bwd_sweep", vasmg.KERNEL_SWEEP)):
+            kms, kb = vasmg.vasmg_time_kernel_multi(s.h, which, l, k, 5)
+            kern[f"{name}_l{l}"] = {"ms": kms, "bytes": kb, "gbs": kb / (kms / 1e3) / 1e9,
+                                    "frac": kb / (kms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    out["launches"] = kern
+    top = max(kern, key=lambda q: kern[q]["ms"])
+    out["roofline"] = {"kernel": top, "achieved": kern[top]["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": kern[top]["frac"], "bytes_per_launch": kern[top]["bytes"], "k": k}
+    return out
+
+
 def ours(args):
     import torch
 
@@ -498,6 +558,11 @@ def ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_ms, e2e_work = reduce_over_ranks(e2e_s * 1e3, float(nfree * e2e_iters), dev)
     e2e = e2e_work / (e2e_ms / 1e3) / 1e6
+    # several right-hand sides per launch (vasmg_solve_multi): 8 loads of
+    # the same mesh solved together against the same 8 solved one by one
+    multi = None
+    if args.precision != "fp64" and world == 1:
+        multi = multi_rhs_run(s, F, n, nfree, 8, dev, peaks)
     levels = [vasmg.vasmg_level_info(s.h, l) for l in range(vasmg.vasmg_num_levels(s.h))]
     lanes = [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)]
     dense = [int(v) for v in s.export(vasmg.EXPORT_DENSE, 0, np.int64)]
@@ -557,8 +622,8 @@ def ours(args):
                          "vcycle": {"ms": vc_ms, "bytes": vc_bytes, "gbs": vc_bytes / (vc_ms / 1e3) / 1e9},
                          "fp64_fma": f64, "spmv64": spmv_roofs},
             "e2e": {"value": e2e, "unit": "MDOF*iter/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
-            "gpu_launches": launches, "clocks": clk, "fp64_path": fp64, "other_workloads": others,
-            "serving": serving}
+            "gpu_launches": launches, "clocks": clk, "fp64_path": fp64, "multi_rhs": multi,
+            "other_workloads": others, "serving": serving}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ns = SAMPLE_N.get(args.workload, 32)
         side = f"{ns}^3" if args.workload.startswith("cube") else f"{ns}x{ns}"

@@ -1,13 +1,14 @@
 // Request server (include/vasmg.h, "serving"): continuous admission of
 // independent problems onto one device.  Host code only; every request runs
-// through the public entry points (vasmg_setup, vasmg_solve, vasmg_destroy),
-// so its result is the one those calls give alone.
+// through the public entry points (vasmg_setup, vasmg_solve_multi,
+// vasmg_destroy), so its result is the one those calls give alone.
 //
 // Worker threads ("slots") each own a non-blocking stream.  A free slot takes
 // the head of the arrival queue once the head's estimated device footprint
 // fits the unused part of the memory budget (the head runs alone if it can
 // never fit).  The slot sets up the request's hierarchy, keeps it resident
-// while it solves every right-hand side, writes U, destroys the hierarchy and
+// while it solves all right-hand sides together (one multi solve), writes U,
+// destroys the hierarchy and
 // returns the footprint to the budget.  Slots run concurrently, so requests
 // overlap on the device; each handle's sweep grids are capped to a share of
 // the device (vasmg_options.max_ctas) so that all running sweeps can be
@@ -54,9 +55,12 @@ struct Request {
 
 // Device bytes a request is expected to hold at its peak (setup sorts and the
 // Galerkin products dominate): per vertex and per element, by dimension.
+// The multi solve holds its right-hand sides in passes of 2, 4 or 8: about
+// 80 bytes per dof and right-hand side of a pass (CG and V-cycle vectors).
 int64_t footprint_estimate(int dim, int64_t nv, int64_t ne, int32_t nrhs) {
   const int64_t per_v = dim == 2 ? 4096 : 16384;
-  return per_v * nv + 96 * ne + 16 * (int64_t)nrhs * nv * dim + (32ll << 20);
+  const int64_t pass = nrhs <= 1 ? 1 : (nrhs <= 2 ? 2 : (nrhs <= 4 ? 4 : 8));
+  return per_v * nv + 96 * ne + (16 * (int64_t)nrhs + 80 * pass) * nv * dim + (32ll << 20);
 }
 
 }  // namespace
@@ -104,19 +108,22 @@ struct vasmg_server {
     st.setup_ms = now_ms() - t0;
     int worst = rc;
     if (rc == VASMG_OK) {
+      // every right-hand side of the request in one multi solve: each sweep
+      // reads the hierarchy once for all of them, and each result is the one
+      // vasmg_solve gives alone
       const double t1 = now_ms();
-      for (size_t i = 0; i < r->F.size(); ++i) {
-        vasmg_stats s{};
-        rc = vasmg_solve(h, r->F[i].data(), r->U[i], o.tol, &s);
-        if (rc < 0) {
-          worst = rc;
-          break;
+      const int32_t k = (int32_t)r->F.size();
+      std::vector<const double*> Fp(k);
+      for (int32_t i = 0; i < k; ++i) Fp[i] = r->F[i].data();
+      std::vector<vasmg_stats> ss(k);
+      rc = vasmg_solve_multi(h, k, Fp.data(), r->U.data(), o.tol, ss.data());
+      worst = rc;
+      if (rc >= 0)
+        for (int32_t i = 0; i < k; ++i) {
+          st.iterations += ss[i].iterations;
+          st.max_iterations = std::max(st.max_iterations, ss[i].iterations);
+          st.max_rel_res = std::max(st.max_rel_res, ss[i].rel_res);
         }
-        worst = std::max(worst, rc);
-        st.iterations += s.iterations;
-        st.max_iterations = std::max(st.max_iterations, s.iterations);
-        st.max_rel_res = std::max(st.max_rel_res, s.rel_res);
-      }
       st.solve_ms = now_ms() - t1;
     }
     if (h) vasmg_destroy(h);

@@ -25,7 +25,7 @@
 
 namespace vasmg {
 
-constexpr int DFM_THREADS = 128;    // threads of the multi sweep CTAs (one CTA per region, as the single sweeps)
+constexpr int DFM_THREADS = 256;    // threads of the multi sweep CTAs (one CTA per region, as the single sweeps)
 constexpr int TAILM_THREADS = 512;  // threads of the multi tail CTAs (more registers per thread than the single tail)
 constexpr int KMAX = 8;             // right-hand sides per pass
 constexpr int KG_SPMV = 4;          // right-hand sides per SpMV launch
@@ -62,11 +62,11 @@ struct RowPFM {
   int cj;
   V a[D * D];
   V di[D];
-  V bv[KR][D];
 };
 
 // Loads what nothing writes during the sweep: the row range, this lane's
-// first entry, the diagonal inverse row and b of every right-hand side.
+// first entry and the diagonal inverse row (b of the right-hand sides is
+// loaded when the row is finished, which keeps the prefetched state small).
 template <int D, int KR, typename V, typename S, int MODE, typename L_t>
 __device__ __forceinline__ void rowm_prefetch(const L_t& L, int row, bool valid, int lane, RowPFM<D, KR, V>& st) {
   st.sg = RowSeg{0, 0, 0, 0};
@@ -83,10 +83,6 @@ __device__ __forceinline__ void rowm_prefetch(const L_t& L, int row, bool valid,
   if (MODE != 2 && valid && lane < D) {
 #pragma unroll
     for (int bb = 0; bb < D; ++bb) st.di[bb] = __ldg((const V*)L.dinv + (long long)(lane * D + bb) * L.nv + row);
-#pragma unroll
-    for (int i = 0; i < KR; ++i)
-#pragma unroll
-      for (int bb = 0; bb < D; ++bb) st.bv[i][bb] = __ldcg((const V*)L.b + ((long long)row * KR + i) * D + bb);
   }
 }
 
@@ -101,6 +97,9 @@ __device__ __forceinline__ void rowm_finish(const L_t& L, int row, bool valid, i
   for (int i = 0; i < KR; ++i)
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[i][a] = V(0);
+  // b of every right-hand side (lanes a < D write the row), in flight while the entries are gathered
+  V bv[KR * D];
+  if (MODE != 2 && valid && lane < D) ld_vec_n<KR * D, false>((const V*)L.b + (long long)row * KR * D, bv);
   if (st.cj >= 0) {
     V xj[KR * D];
     ld_vec_n<KR * D, gather_l1<L_t, false>()>((const V*)L.x + (long long)st.cj * KR * D, xj);
@@ -147,7 +146,7 @@ __device__ __forceinline__ void rowm_finish(const L_t& L, int row, bool valid, i
     } else {
       V s = V(0);
 #pragma unroll
-      for (int bb = 0; bb < D; ++bb) s += st.di[bb] * (st.bv[i][bb] - acc[i][bb]);
+      for (int bb = 0; bb < D; ++bb) s += st.di[bb] * (bv[i * D + bb] - acc[i][bb]);
       __stcg((V*)L.x + ((long long)row * KR + i) * D + lane, s);
     }
   }
@@ -721,8 +720,8 @@ template <int D, typename S>
 struct MultiEngine : MultiBase {
   using V = float;
   EngineView<V> v;
-  bool allocated = false;
-  std::vector<DevBuf<V>> xm, bm, rm;  // per level, [nv][KMAX][D] (a pass with KR uses the first nv KR D)
+  int cap = 0;                        // right-hand sides the buffers hold (2, 4 or 8)
+  std::vector<DevBuf<V>> xm, bm, rm;  // per level, [nv][cap][D] (a pass with KR uses the first nv KR D)
   DevBuf<double> U, r, p, q, Fb, Ub, part, hist;
   DevBuf<Scalars> sc;
   DevBuf<int> ctl;
@@ -750,14 +749,22 @@ struct MultiEngine : MultiBase {
   static int slot(int KR) { return KR == 2 ? 1 : (KR == 4 ? 2 : 3); }
   i64 n0() const { return v.nv[0] * D; }
 
-  void allocate() {
-    if (allocated) return;
+  // Buffers for passes of up to kr right-hand sides; growing them drops the
+  // graphs captured with the old ones.
+  void allocate(int kr) {
+    if (kr <= cap) return;
+    for (int t = 0; t < 4; ++t) {
+      if (exec_while[t]) cudaGraphExecDestroy(exec_while[t]);
+      if (exec_body[t]) cudaGraphExecDestroy(exec_body[t]);
+      exec_while[t] = exec_body[t] = nullptr;
+    }
     cudaStream_t s = v.stream;
+    VASMG_CUDA(cudaStreamSynchronize(s));
     xm.resize(v.L);
     bm.resize(v.L);
     rm.resize(v.L);
     for (int l = 0; l < v.L; ++l) {
-      const i64 n = std::max<i64>(1, v.nv[l] * D * KMAX);
+      const i64 n = std::max<i64>(1, v.nv[l] * D * kr);
       xm[l].alloc(n, s);
       bm[l].alloc(n, s);
       rm[l].alloc(n, s);
@@ -766,17 +773,17 @@ struct MultiEngine : MultiBase {
       rm[l].zero();
     }
     const i64 n = n0();
-    U.alloc(n * KMAX, s);
-    r.alloc(n * KMAX, s);
-    p.alloc(n * KMAX, s);
-    q.alloc(n * KMAX, s);
-    Fb.alloc(n * KMAX, s);
-    Ub.alloc(n * KMAX, s);
+    U.alloc(n * kr, s);
+    r.alloc(n * kr, s);
+    p.alloc(n * kr, s);
+    q.alloc(n * kr, s);
+    Fb.alloc(n * kr, s);
+    Ub.alloc(n * kr, s);
     p.zero();
     pstride = std::max(v.cg_blocks, v.spmv_blocks);
-    part.alloc((i64)pstride * KMAX, s);
-    hist.alloc((i64)std::max(1, v.max_iters) * KMAX, s);
-    sc.alloc(KMAX, s);
+    part.alloc((i64)pstride * kr, s);
+    hist.alloc((i64)std::max(1, v.max_iters) * kr, s);
+    sc.alloc(kr, s);
     sc.zero();
     ctl.alloc(2, s);
     ctl.zero();
@@ -784,10 +791,10 @@ struct MultiEngine : MultiBase {
     const TailArgs<V>& ta = v.ta;
     i64 slen = 1;
     if (ta.kd > ta.ls) slen = ta.soff[ta.kd] - ta.soff[ta.ls];
-    stash.alloc(std::max<i64>(1, slen) * KMAX, s);
-    VASMG_CUDA(cudaMallocHost((void**)&host_sc, sizeof(Scalars) * KMAX));
-    VASMG_CUDA(cudaMallocHost((void**)&host_ctl, sizeof(int) * 2));
-    allocated = true;
+    stash.alloc(std::max<i64>(1, slen) * kr, s);
+    if (!host_sc) VASMG_CUDA(cudaMallocHost((void**)&host_sc, sizeof(Scalars) * KMAX));
+    if (!host_ctl) VASMG_CUDA(cudaMallocHost((void**)&host_ctl, sizeof(int) * 2));
+    cap = kr;
   }
 
   // level l's view with the multi vectors of KR right-hand sides
@@ -1105,7 +1112,7 @@ struct MultiEngine : MultiBase {
   }
 
   int solve(int k, const double* const* F, double* const* Uo, double tol, vasmg_stats* st, i64* launches) override {
-    allocate();
+    allocate(k <= 2 ? 2 : (k <= 4 ? 4 : KMAX));
     int worst = VASMG_OK;
     for (int c0 = 0; c0 < k; c0 += KMAX) {
       const int kc = std::min(KMAX, k - c0);
@@ -1199,7 +1206,7 @@ struct MultiEngine : MultiBase {
     return (double)ms / reps;
   }
   double time(int which, int level, int k, int reps, double* bytes) override {
-    allocate();
+    allocate(k);
     switch (k) {
       case 2: return time_k<2>(which, level, reps, bytes);
       case 4: return time_k<4>(which, level, reps, bytes);

@@ -111,6 +111,19 @@ typedef struct {
                                   same bits.  0: lanes per row by rule from the
                                   mean row length. */
   void* stream;                /* cudaStream_t used for all device work */
+  int32_t cycle;               /* coarse corrections per level, gamma: 1 (default)
+                                  the V-cycle of Alg. 3, 2 the W-cycle of Fig. 2
+                                  (every level above the second-coarsest solves
+                                  its coarse problem by two cycles, the second on
+                                  the updated coarse residual), up to 4.  gamma >= 2
+                                  runs every level with per-level launches (no
+                                  cluster tail, no dense level) */
+  int32_t additive;            /* 1: the preconditioner is the additive form of
+                                  Sec. 4, B = S + P B_1 P^T: S one forward and one
+                                  backward multicolour sweep from zero on the fine
+                                  level, B_1 the cycle above from level 1 (the
+                                  coarsest solve when level 1 is the coarsest);
+                                  0 (default): the cycle from the fine level */
 } vasmg_options;
 
 typedef struct {
@@ -178,6 +191,8 @@ int vasmg_solve(vasmg_handle h, const double* F, double* U, double tol, vasmg_st
  * that pass's vectors and graph.  Returns the most severe status. */
 int vasmg_solve_multi(vasmg_handle h, int32_t k, const double* const* F, double* const* U, double tol,
                       vasmg_stats* st);
+/* (With vasmg_options.cycle > 1 or .additive, the k solves also run one after
+ * another.) */
 
 /* Solve k independent systems (uneven sizes allowed), each to tol, sharing
  * the device; h[i] may repeat.  st may be NULL or an array of k stats.
@@ -295,7 +310,9 @@ int vasmg_export(vasmg_handle h, int32_t what, int32_t level, void* buf, int64_t
  *   VASMG_OP_RESTRICT    y = R x (level l -> l+1, y has nv_{l+1}*dim entries)
  *   VASMG_OP_PROLONG     y += P x (level l+1 -> l, x has nv_{l+1}*dim entries)
  *   VASMG_OP_COARSE      y = A_L^{-1} x on the coarsest level (Cholesky)
- *   VASMG_OP_VCYCLE      y = M x, one V-cycle from level l down */
+ *   VASMG_OP_VCYCLE      y = M x, one cycle (V, or gamma of vasmg_options.cycle) from level l down
+ *   VASMG_OP_PRECOND     y = B x, the preconditioner PCG applies (the options' cycle from level 0,
+ *                        or the additive form); level must be 0 */
 enum {
   VASMG_OP_MATVEC = 0,
   VASMG_OP_SMOOTH_FWD = 1,
@@ -304,7 +321,8 @@ enum {
   VASMG_OP_RESTRICT = 4,
   VASMG_OP_PROLONG = 5,
   VASMG_OP_COARSE = 6,
-  VASMG_OP_VCYCLE = 7
+  VASMG_OP_VCYCLE = 7,
+  VASMG_OP_PRECOND = 8
 };
 int vasmg_apply(vasmg_handle h, int32_t op, int32_t level, const double* x, double* y);
 

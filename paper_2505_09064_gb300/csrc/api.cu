@@ -138,6 +138,8 @@ int vasmg_default_options(int dim, vasmg_options* out) {
   out->dense_coarse = 1;
   out->autotune = 1;
   out->stream = nullptr;
+  out->cycle = 1;
+  out->additive = 0;
   return VASMG_OK;
 }
 
@@ -155,7 +157,8 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   if (o.n_pre != 1 || o.n_post != 1) return VASMG_ERR_UNSUPPORTED;
   if (o.precision < VASMG_FP64 || o.precision > VASMG_FP32_VCYCLE_BF16_SMOOTH) return VASMG_ERR_INVALID_ARG;
   if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096 || o.max_iters <= 0 || o.max_ctas < 0 ||
-      o.dense_coarse < 0 || o.dense_coarse > 1 || o.autotune < 0 || o.autotune > 1)
+      o.dense_coarse < 0 || o.dense_coarse > 1 || o.autotune < 0 || o.autotune > 1 || o.cycle < 0 ||
+      o.cycle > 4 || o.additive < 0 || o.additive > 1)
     return VASMG_ERR_INVALID_ARG;
   vasmg_ctx* h = new vasmg_ctx();
   struct Guard {
@@ -177,6 +180,8 @@ int vasmg_setup(const vasmg_problem* pb, const vasmg_options* opt, vasmg_handle*
   c.max_ctas = o.max_ctas > 0 ? o.max_ctas : 0;
   c.dense_coarse = o.dense_coarse;
   c.autotune = o.autotune;
+  c.gamma = o.cycle > 0 ? o.cycle : 1;
+  c.additive = o.additive;
   c.coarse_max_dofs = o.coarse_max_dofs;
   c.user_stream = (cudaStream_t)o.stream;
   VASMG_CUDA(cudaGetDevice(&c.device));

@@ -183,6 +183,8 @@ struct Ctx {
   int max_ctas = 0;       // cap on the CTAs of one sweep launch (0: device capacity)
   int dense_coarse = 1;   // FP32-vector modes: apply the cycle below the dense level as one matrix
   int autotune = 1;       // measure the lanes per row of each region level at setup
+  int gamma = 1;          // coarse corrections per level (1: V-cycle, 2: W-cycle)
+  int additive = 0;       // preconditioner S + P B_1 P^T (Sec. 4) instead of the cycle from level 0
   int ctas_used = 0;      // largest sweep grid this handle launches
   int cta_capacity = 0;   // CTAs of the sweep kernels the device holds at once
   i64 coarse_max_dofs = 0;

@@ -506,17 +506,19 @@ void solve_level_values(Ctx& c) {
                                                                            sl.off16.get());
       check_launch("planes16");
     }
-    if (l == 0) ensure(sl.diag64, (i64)dd * cl.nv);
+    // level 0 (the SELL operator) and, for the W-cycle's coarse residuals, every level
+    const bool keep_diag = l == 0 || c.gamma >= 2;
+    if (keep_diag) ensure(sl.diag64, (i64)dd * cl.nv);
     ensure(sl.dinv64, (i64)dd * cl.nv);
     ensure(sl.dinv32, (i64)dd * cl.nv);
     ensure(cl.dinv, (i64)dd * cl.nv);
     if (d == 2)
       diag_kernel<2><<<grid_for(cl.nv, 256), 256, 0, s>>>(cl.rp.get(), cl.ci.get(), cl.v.get(), sl.perm.get(), cl.nv,
-                                                           l == 0 ? sl.diag64.get() : nullptr, sl.dinv64.get(),
+                                                           keep_diag ? sl.diag64.get() : nullptr, sl.dinv64.get(),
                                                            sl.dinv32.get(), cl.dinv.get());
     else
       diag_kernel<3><<<grid_for(cl.nv, 256), 256, 0, s>>>(cl.rp.get(), cl.ci.get(), cl.v.get(), sl.perm.get(), cl.nv,
-                                                           l == 0 ? sl.diag64.get() : nullptr, sl.dinv64.get(),
+                                                           keep_diag ? sl.diag64.get() : nullptr, sl.dinv64.get(),
                                                            sl.dinv32.get(), cl.dinv.get());
     check_launch("diag");
   }

@@ -145,6 +145,52 @@ __global__ void sell_fill_kernel(const int* __restrict__ rows, const int* __rest
   }
 }
 
+// ------------------------------------------------------------------ cycle variants (W-cycle, additive form)
+
+// out = bs - A x on one level, every block of each row (the diagonal one from
+// the FP64 diagonal planes): the coarse residual on which the W-cycle's
+// second coarse cycle runs.  G lanes per row as in the residual kernel.
+template <int D, int G, typename V, typename S>
+__global__ void __launch_bounds__(256) full_residual_kernel(const __grid_constant__ LV<V> L,
+                                                            const double* __restrict__ diag,
+                                                            const V* __restrict__ bs, V* __restrict__ out) {
+  constexpr int NG = 256 / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  for (int base = blockIdx.x * NG; base < L.nv; base += gridDim.x * NG) {
+    const int row = base + g;
+    const bool valid = row < L.nv;
+    RowSeg sg{0, 0, 0, 0};
+    if (valid) sg = seg_range<1>(L, row);
+    V acc[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] = V(0);
+    row_entries<D, G, V, S, 1, false, true>(L, sg, lane, acc);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o, G);
+    if (valid && lane < D) {
+      V dx = V(0);
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb)
+        dx += (V)__ldg(diag + (long long)(lane * D + bb) * L.nv + row) * __ldcg((const V*)L.x + (long long)row * D + bb);
+      out[(long long)row * D + lane] = bs[(long long)row * D + lane] - (pick<D>(acc, lane) + dx);
+    }
+  }
+}
+
+template <typename V>
+__global__ void vcopy_kernel(V* __restrict__ dst, const V* __restrict__ src, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    dst[t] = src[t];
+}
+
+template <typename V>
+__global__ void vadd_kernel(V* __restrict__ dst, const V* __restrict__ src, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    dst[t] += src[t];
+}
+
 // ------------------------------------------------------------------ conversions for vasmg_apply
 
 template <typename V>
@@ -278,6 +324,9 @@ struct Engine : EngineBase {
   i64 launches_body = 0;
   i64 launch_counter = 0;
   MultiBase* multi = nullptr;  // several right-hand sides (FP32-vector modes), made on first use
+  // gamma-cycle (gamma >= 2): each level's coarse right-hand side and first
+  // coarse correction, kept while the next coarse cycle runs
+  std::vector<DevBuf<V>> wb, we;
 
   explicit Engine(Ctx& ctx) : c(&ctx) { build(); }
   ~Engine() override {
@@ -633,6 +682,14 @@ struct Engine : EngineBase {
     cga.sc = sc.get();
     cga.cond = 0;
     build_sell();
+    if (c->gamma >= 2) {
+      wb.resize(L);
+      we.resize(L);
+      for (int l = 1; l < L; ++l) {
+        wb[l].alloc(std::max<i64>(1, c->S[l].nv * D), s);
+        we[l].alloc(std::max<i64>(1, c->S[l].nv * D), s);
+      }
+    }
     if (c->autotune) autotune_lanes();
     VASMG_CUDA(cudaStreamSynchronize(s));
   }
@@ -835,7 +892,9 @@ struct Engine : EngineBase {
   void build_dense_level() {
     kd = -1;
     dn = 0;
-    if (!c->dense_coarse) return;
+    // the dense matrix is the V-cycle below its level; gamma >= 2 runs every
+    // level with per-level launches instead
+    if (!c->dense_coarse || c->gamma >= 2) return;
     if constexpr (std::is_same<V, float>::value) {
       const int ls = one_cta_start(lt);
       for (int l = ls; l < L; ++l) {
@@ -909,6 +968,72 @@ struct Engine : EngineBase {
     for (int l = lt - 1; l >= l0; --l) up(l, 3, s);
   }
 
+  void vec_copy(V* dst, const V* src, i64 n, cudaStream_t s) {
+    vcopy_kernel<V><<<plain_grid(n), 256, 0, s>>>(dst, src, n);
+    ++launch_counter;
+  }
+  void vec_add(V* dst, const V* src, i64 n, cudaStream_t s) {
+    vadd_kernel<V><<<plain_grid(n), 256, 0, s>>>(dst, src, n);
+    ++launch_counter;
+  }
+  // b_l = bs - A_l x_l
+  void full_residual(int l, const V* bs, cudaStream_t s) {
+    const double* dg = c->S[l].diag64.get();
+    const int grid = plain_grid((i64)lv[l].nv * G[l]);
+    switch (G[l]) {
+      case 4: full_residual_kernel<D, 4, V, S><<<grid, 256, 0, s>>>(lv[l], dg, bs, lv[l].b); break;
+      case 8: full_residual_kernel<D, 8, V, S><<<grid, 256, 0, s>>>(lv[l], dg, bs, lv[l].b); break;
+      case 16: full_residual_kernel<D, 16, V, S><<<grid, 256, 0, s>>>(lv[l], dg, bs, lv[l].b); break;
+      default: full_residual_kernel<D, 32, V, S><<<grid, 256, 0, s>>>(lv[l], dg, bs, lv[l].b); break;
+    }
+    ++launch_counter;
+  }
+  // The cycle with gamma coarse corrections from level l (b_l set, result in
+  // x_l), one launch per step and level: zero start, forward sweep, residual,
+  // restriction; the coarse problem by gamma cycles, each after the first on
+  // the updated coarse residual (one only when the coarser level is the
+  // coarsest, which is solved directly); prolongation, backward sweep.
+  void gcycle(int l, cudaStream_t s) {
+    if (l == L - 1) {
+      coarse_kernel<V><<<1, 32, 0, s>>>(co, lv[L - 1].b, lv[L - 1].x);
+      ++launch_counter;
+      return;
+    }
+    down(l, 7, s);
+    gcycle(l + 1, s);
+    const int reps = l + 2 == L ? 1 : c->gamma;
+    if (reps > 1) {
+      const i64 nc = (i64)lv[l + 1].nv * D;
+      vec_copy(wb[l + 1].get(), lv[l + 1].b, nc, s);
+      for (int rep = 1; rep < reps; ++rep) {
+        vec_copy(we[l + 1].get(), lv[l + 1].x, nc, s);
+        full_residual(l + 1, wb[l + 1].get(), s);
+        gcycle(l + 1, s);
+        vec_add(lv[l + 1].x, we[l + 1].get(), nc, s);
+      }
+    }
+    up(l, 3, s);
+  }
+  void cycle_from(int l, cudaStream_t s) {
+    if (c->gamma >= 2) gcycle(l, s);
+    else vcycle(l, s);
+  }
+  // The preconditioner: the cycle from level 0, or the additive form of
+  // Sec. 4, x_0 = S b_0 + P B_1 R b_0 (S: forward then backward sweep from
+  // zero; B_1: the cycle from level 1).
+  void precond(cudaStream_t s) {
+    if (!c->additive || L == 1) {
+      cycle_from(0, s);
+      return;
+    }
+    vec_copy(lv[0].r, lv[0].b, (i64)lv[0].nv * D, s);
+    down(0, 4, s);   // b_1 = R b_0
+    cycle_from(1, s);
+    down(0, 1, s);   // x_0 = forward sweep from zero
+    up(0, 2, s);     // backward sweep
+    up(0, 1, s);     // x_0 += P x_1
+  }
+
   void spmv(cudaStream_t s, int with_dot) {
     if (cga.cond)
       spmv_sell_kernel<D, true><<<spmv_blocks, CG_THREADS, 0, s>>>(cga, with_dot);
@@ -921,7 +1046,7 @@ struct Engine : EngineBase {
   // p = z + beta p; q = A p, alpha; U, r update + stop test.
   void body(cudaStream_t s) {
     V* z = lv[0].x;
-    vcycle(0, s);
+    precond(s);
     if (cga.cond)
       rz_kernel<D, V, true><<<cg_blocks, CG_THREADS, 0, s>>>(cga, z);
     else
@@ -1107,13 +1232,17 @@ struct Engine : EngineBase {
   }
   int solve_multi(Ctx& ctx, int k, const double* const* F, double* const* Uo, double tol, vasmg_stats* st) override {
     if (k == 1) return solve(ctx, F[0], Uo[0], tol, st);
+    const bool variant = c->gamma != 1 || c->additive;
     if constexpr (std::is_same<V, float>::value) {
-      i64 launches = 0;
-      const int rc = get_multi()->solve(k, F, Uo, tol, st, &launches);
-      ctx.last_launches = launches;
-      return rc;
-    } else {
-      // the FP64 V-cycle: one solve after another
+      if (!variant) {
+        i64 launches = 0;
+        const int rc = get_multi()->solve(k, F, Uo, tol, st, &launches);
+        ctx.last_launches = launches;
+        return rc;
+      }
+    }
+    {
+      // the FP64 V-cycle and the cycle variants: one solve after another
       int worst = VASMG_OK;
       i64 launches = 0;
       for (int i = 0; i < k; ++i) {
@@ -1205,8 +1334,14 @@ struct Engine : EngineBase {
         break;
       case VASMG_OP_VCYCLE:
         to_solve(x, lv[l].b, l, s);
-        vcycle(l, s);
+        cycle_from(l, s);
         from_solve(lv[l].x, y, l, s);
+        break;
+      case VASMG_OP_PRECOND:
+        VASMG_CHECK(l == 0, VASMG_ERR_INVALID_ARG, "the preconditioner acts on level 0");
+        to_solve(x, lv[0].b, 0, s);
+        precond(s);
+        from_solve(lv[0].x, y, 0, s);
         break;
       default:
         throw Error(VASMG_ERR_INVALID_ARG, "unknown op");

@@ -24,7 +24,7 @@ PRECISIONS = {"fp64": VASMG_FP64, "fp32": VASMG_FP32_VCYCLE, "bf16": VASMG_FP32_
 (EXPORT_MORTON, EXPORT_LEAF, EXPORT_CELLS, EXPORT_LATTICE, EXPORT_P_RP, EXPORT_P_CI, EXPORT_P_W, EXPORT_A_RP,
  EXPORT_A_CI, EXPORT_A_V, EXPORT_DEAD, EXPORT_COLOUR, EXPORT_DINV, EXPORT_BOX, EXPORT_LIFT, EXPORT_VOL,
  EXPORT_DENSE, EXPORT_LANES) = (0, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18)
-OP_MATVEC, OP_SMOOTH_FWD, OP_SMOOTH_BWD, OP_RESIDUAL, OP_RESTRICT, OP_PROLONG, OP_COARSE, OP_VCYCLE = range(8)
+OP_MATVEC, OP_SMOOTH_FWD, OP_SMOOTH_BWD, OP_RESIDUAL, OP_RESTRICT, OP_PROLONG, OP_COARSE, OP_VCYCLE, OP_PRECOND = range(9)
 KERNEL_SPMV64, KERNEL_SWEEP, KERNEL_VCYCLE, KERNEL_DOWN, KERNEL_UP = 0, 1, 2, 3, 4
 KERNEL_FWD_SWEEP, KERNEL_RESIDUAL, KERNEL_RESTRICT, KERNEL_PROLONG, KERNEL_TAIL = 5, 6, 7, 8, 9
 
@@ -51,7 +51,7 @@ class vasmg_options(C.Structure):
     _fields_ = [("leaf_threshold", C.c_int32), ("n_pre", C.c_int32), ("n_post", C.c_int32),
                 ("precision", C.c_int32), ("coarse_max_dofs", C.c_int64), ("max_iters", C.c_int32),
                 ("use_graph", C.c_int32), ("max_ctas", C.c_int32), ("dense_coarse", C.c_int32),
-                ("autotune", C.c_int32), ("stream", C.c_void_p)]
+                ("autotune", C.c_int32), ("stream", C.c_void_p), ("cycle", C.c_int32), ("additive", C.c_int32)]
 
 
 class vasmg_server_opts(C.Structure):
@@ -350,7 +350,7 @@ class Solver:
 
     def __init__(self, prob: dict, precision: str = "fp64", stream=None, threshold: int = 0,
                  coarse_max_dofs: int = 0, max_iters: int = 1000, use_graph: bool = True, max_ctas: int = 0,
-                 dense_coarse: bool = True, autotune: bool = True):
+                 dense_coarse: bool = True, autotune: bool = True, cycle: int = 1, additive: bool = False):
         self.dim = int(prob["dim"])
         self.n = int(np.asarray(prob["coords"]).shape[0]) * self.dim
         o = vasmg_default_options(self.dim)
@@ -363,6 +363,8 @@ class Solver:
         o.max_ctas = max_ctas
         o.dense_coarse = 1 if dense_coarse else 0
         o.autotune = 1 if autotune else 0
+        o.cycle = int(cycle)
+        o.additive = 1 if additive else 0
         o.stream = C.c_void_p(stream) if isinstance(stream, int) else stream
         self.options = o
         self.h = vasmg_setup(prob, o)

@@ -194,15 +194,29 @@ int vasmg_solve_multi(vasmg_handle h, int32_t k, const double* const* F, double*
 /* (With vasmg_options.cycle > 1 or .additive, the k solves also run one after
  * another.) */
 
-/* Solve k independent systems (uneven sizes allowed), each to tol, sharing
- * the device; h[i] may repeat.  st may be NULL or an array of k stats.
+/* Solve k independent systems (uneven sizes allowed, 2D and 3D mixed), each
+ * to tol, sharing the device; h[i] may repeat.  st may be NULL or an array of
+ * k stats.
  *
- * The solves run concurrently, one host thread and one stream per handle, in
- * groups whose sweep grids (vasmg_options.max_ctas, as set up) fit the device
- * together: every CTA of a running sweep launch must be resident at once.
- * Handles set up with max_ctas = 0 fill the device and run one at a time.  A
- * handle that appears twice runs in two different groups.  Each result is
- * the one vasmg_solve gives alone.  Returns the most severe status. */
+ * When the handles are distinct, on the current device, set up with one
+ * FP32-vector precision (VASMG_FP32_VCYCLE or ..._BF16_SMOOTH) and the plain
+ * V-cycle, the k PCG solves advance together with one launch per level and
+ * phase for all of them: each region level's forward sweeps, residuals,
+ * restrictions, prolongations and backward sweeps of every handle in one
+ * launch (a CTA per region of each), every handle's small levels in one
+ * launch (a thread-block cluster each), and every CG kernel for all handles
+ * in one launch.  A level's regions of all handles must be resident at once:
+ * handles whose regions (vasmg_options.max_ctas, as set up) do not fit the
+ * device together run in successive groups of such launches.
+ *
+ * Otherwise the solves run concurrently, one host thread and one stream per
+ * handle, in groups whose sweep grids fit the device together; handles set
+ * up with max_ctas = 0 then run one at a time, and a handle that appears
+ * twice runs in two different groups.
+ *
+ * Either way each result is the one vasmg_solve gives alone (the same
+ * arithmetic for every row and reduction).  vasmg_last_launch_count of each
+ * handle reports the batch's launches.  Returns the most severe status. */
 int vasmg_solve_batch(int32_t k, const vasmg_handle* h, const double* const* F, double* const* U, double tol,
                       vasmg_stats* st);
 

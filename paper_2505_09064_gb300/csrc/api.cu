@@ -332,9 +332,38 @@ int vasmg_solve_multi(vasmg_handle h, int32_t k, const double* const* F, double*
 
 int vasmg_solve_batch(int32_t k, const vasmg_handle* h, const double* const* F, double* const* U, double tol,
                       vasmg_stats* st) {
-  if (k < 0 || (k > 0 && (!h || !F || !U))) return VASMG_ERR_INVALID_ARG;
+  if (k < 0 || (k > 0 && (!h || !F || !U)) || !(tol > 0.0)) return VASMG_ERR_INVALID_ARG;
   for (int32_t i = 0; i < k; ++i)
     if (!h[i] || !F[i] || !U[i]) return VASMG_ERR_INVALID_ARG;
+  // handles that can share launches: one launch per level and phase for all
+  {
+    int rc = -1000;
+    const double t0 = now_ms();
+    try {
+      std::vector<Ctx*> cs;
+      for (int32_t i = 0; i < k; ++i) cs.push_back(&h[i]->c);
+      rc = solve_batch_dev(cs, F, U, tol, st, nullptr);
+    } catch (const std::bad_alloc& e) {
+      g_last_error = e.what();
+      return VASMG_ERR_OOM;
+    } catch (const std::exception& e) {
+      return fail(e);
+    }
+    if (rc != -1000) {
+      if (st) {
+        const double ms = now_ms() - t0;
+        for (int32_t i = 0; i < k; ++i) {
+          const Ctx& c = h[i]->c;
+          double nb0 = (double)c.C[0].nnzb, tot = 0;
+          for (auto& l : c.C) tot += (double)l.nnzb;
+          st[i].solve_ms = ms;
+          st[i].setup_ms = c.setup_ms;
+          st[i].op_complexity = tot / nb0;
+        }
+      }
+      return rc;
+    }
+  }
   // groups of handles whose sweep grids are resident together
   int cap = 0;
   for (int32_t i = 0; i < k; ++i) {

@@ -251,6 +251,8 @@ int solve_dev(Ctx& c, const double* F_dev, double* U_dev, double tol, vasmg_stat
 void apply_op(Ctx& c, int op, int level, const double* x_dev, double* y_dev);
 double time_kernel(Ctx& c, int which, int level, int reps, double* bytes);
 int solve_multi_dev(Ctx& c, int k, const double* const* F, double* const* U, double tol, vasmg_stats* st);
+int solve_batch_dev(const std::vector<Ctx*>& cs, const double* const* F, double* const* U, double tol,
+                    vasmg_stats* st, i64* launches);
 double time_kernel_multi(Ctx& c, int which, int level, int k, int reps, double* bytes);
 void dense_level_info(Ctx& c, int* kd, int* dn);  // the engine's dense level, (-1, 0) if none
 void lanes_info(Ctx& c, int32_t* g, int n);       // lanes per row of the region levels, 0 elsewhere

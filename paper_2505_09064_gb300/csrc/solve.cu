@@ -255,6 +255,10 @@ struct EngineBase {
   // k right-hand sides on this hierarchy (solve_multi.cu for the FP32-vector modes)
   virtual int solve_multi(Ctx& c, int k, const double* const* F, double* const* U, double tol, vasmg_stats* st) = 0;
   virtual double time_multi(Ctx& c, int which, int level, int k, int reps, double* bytes) = 0;
+  // the engine's view for a batched launch; false unless the V-cycle has FP32
+  // vectors and is the plain V-cycle
+  virtual bool batch_view(EngineView<float>* v) = 0;
+  virtual int storage() const = 0;  // 0 FP64, 1 FP32, 2 BF16 operator values
 };
 
 // Lanes per row measured rather than picked by rule (vasmg_options.autotune):
@@ -1220,6 +1224,10 @@ struct Engine : EngineBase {
     v.spmv_blocks = spmv_blocks;
     v.sell_real_entries = sell_real_entries;
     v.ctr = ctrs.get();
+    v.dim = D;
+    v.device = c->device;
+    v.Fbuf = Fbuf.get();
+    v.Ubuf = Ubuf.get();
     return v;
   }
   MultiBase* get_multi() {
@@ -1254,6 +1262,18 @@ struct Engine : EngineBase {
       ctx.last_launches = launches;
       return worst;
     }
+  }
+  bool batch_view(EngineView<float>* out) override {
+    if constexpr (std::is_same<V, float>::value) {
+      if (c->gamma != 1 || c->additive) return false;
+      *out = view();
+      return true;
+    }
+    (void)out;
+    return false;
+  }
+  int storage() const override {
+    return std::is_same<S, double>::value ? 0 : (std::is_same<S, float>::value ? 1 : 2);
   }
   double time_multi(Ctx& ctx, int which, int level, int k, int reps, double* bytes) override {
     (void)ctx;
@@ -1512,6 +1532,84 @@ double time_kernel(Ctx& c, int which, int level, int reps, double* bytes) {
 
 int solve_multi_dev(Ctx& c, int k, const double* const* F, double* const* U, double tol, vasmg_stats* st) {
   return c.eng->solve_multi(c, k, F, U, tol, st);
+}
+
+// The batched launch of vasmg_solve_batch, or -1000 if these handles cannot
+// share launches (the caller then overlaps single solves): all with FP32
+// vectors, one storage precision, the plain V-cycle, the current device.
+// Handles whose regions do not fit the device together run in successive
+// groups, each one launch per level and phase.
+int solve_batch_dev(const std::vector<Ctx*>& cs, const double* const* F, double* const* U, double tol,
+                    vasmg_stats* st, i64* launches) {
+  const int k = (int)cs.size();
+  if (k < 2) return -1000;
+  int dev = 0;
+  VASMG_CUDA(cudaGetDevice(&dev));
+  const int sto = cs[0]->eng->storage();
+  std::vector<EngineView<float>> views(k);
+  for (int i = 0; i < k; ++i) {
+    if (cs[i]->device != dev || cs[i]->eng->storage() != sto || !cs[i]->eng->batch_view(&views[i])) return -1000;
+    for (int j = 0; j < i; ++j)
+      if (cs[j] == cs[i]) return -1000;
+  }
+  const int cap = sto == 1 ? batch_sweep_capacity<float>() : batch_sweep_capacity<__nv_bfloat16>();
+  for (const auto& v : views)
+    for (int l = 0; l < v.lt; ++l)
+      if (v.lv[l].R > cap) return -1000;
+  // every handle's earlier work first
+  for (Ctx* c : cs) {
+    join_user(*c);
+    VASMG_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  // groups: first fit on the per-level region sums
+  std::vector<std::vector<int>> groups;
+  std::vector<std::vector<int>> load;
+  for (int i = 0; i < k; ++i) {
+    bool placed = false;
+    for (size_t g = 0; g < groups.size() && !placed; ++g) {
+      bool fits = true;
+      for (int l = 0; l < views[i].lt && fits; ++l)
+        fits = (l < (int)load[g].size() ? load[g][l] : 0) + views[i].lv[l].R <= cap;
+      if (fits) {
+        groups[g].push_back(i);
+        if ((int)load[g].size() < views[i].lt) load[g].resize(views[i].lt, 0);
+        for (int l = 0; l < views[i].lt; ++l) load[g][l] += views[i].lv[l].R;
+        placed = true;
+      }
+    }
+    if (!placed) {
+      groups.push_back({i});
+      load.push_back(std::vector<int>(views[i].lt));
+      for (int l = 0; l < views[i].lt; ++l) load.back()[l] = views[i].lv[l].R;
+    }
+  }
+  int worst = VASMG_OK;
+  i64 total = 0;
+  cudaStream_t s = cs[0]->stream;
+  for (const auto& g : groups) {
+    std::vector<EngineView<float>> gv;
+    std::vector<const double*> gF;
+    std::vector<double*> gU;
+    std::vector<vasmg_stats> gst(g.size());
+    for (int i : g) {
+      gv.push_back(views[i]);
+      gF.push_back(F[i]);
+      gU.push_back(U[i]);
+      if (st) gst[gv.size() - 1] = st[i];
+    }
+    i64 nl = 0;
+    const int rc = sto == 1 ? batch_solve<float>(gv, s, gF.data(), gU.data(), tol, st ? gst.data() : nullptr, &nl)
+                            : batch_solve<__nv_bfloat16>(gv, s, gF.data(), gU.data(), tol, st ? gst.data() : nullptr,
+                                                         &nl);
+    total += nl;
+    if (st)
+      for (size_t q = 0; q < g.size(); ++q) st[g[q]] = gst[q];
+    if (rc < 0) worst = std::min(worst, rc);
+    else if (worst >= 0) worst = std::max(worst, rc);
+  }
+  for (Ctx* c : cs) c->last_launches = total;
+  if (launches) *launches = total;
+  return worst;
 }
 
 double time_kernel_multi(Ctx& c, int which, int level, int k, int reps, double* bytes) {

@@ -511,12 +511,14 @@ __device__ __forceinline__ void publish_stage(unsigned long long* f, unsigned ep
   if (threadIdx.x == 0) st_release64(f, ((unsigned long long)epoch << 32) | stage);
 }
 
-// The last CTA to leave advances the launch's epoch.
-__device__ __forceinline__ void leave(int* ctr, int exit_i, int epoch_i) {
+// The last CTA to leave advances the launch's epoch (nctas: the CTAs sharing
+// these counters; the grid unless several levels share one launch).
+__device__ __forceinline__ void leave(int* ctr, int exit_i, int epoch_i, int nctas = -1) {
   __syncthreads();
+  if (nctas < 0) nctas = (int)gridDim.x;
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(ctr + exit_i, 1) == (int)gridDim.x - 1) {
+    if (atomicAdd(ctr + exit_i, 1) == nctas - 1) {
       ctr[exit_i] = 0;
       ctr[epoch_i] += 1;
       __threadfence();
@@ -916,7 +918,7 @@ __device__ void tail_dense_part(const TailArgs<V>& A, int rank, int nct) {
 // so the sub-warp shuffles stay converged.  The smallest levels (ls..L) run
 // on CTA 0 alone between two cluster barriers.
 template <int D, typename V, typename S>
-__global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constant__ TailArgs<V> A) {
+__device__ __forceinline__ void tail_run(const TailArgs<V>& A) {
   constexpr int G = tail_g<D>();
   const int nct = (int)cluster_size(), rank = (int)cluster_rank();
   const int ng = blockDim.x / G;
@@ -947,6 +949,11 @@ __global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constan
     cluster_sync_all();
     tail_sweep<D, G, V, S, 1, false>(L, gg, NG, lane, ClusterSync());
   }
+}
+
+template <int D, typename V, typename S>
+__global__ void __launch_bounds__(TAIL_THREADS) tail_kernel(const __grid_constant__ TailArgs<V> A) {
+  tail_run<D, V, S>(A);
 }
 
 // The dense level's matrix, column by column: CTA j runs the one-CTA V-cycle
@@ -1014,22 +1021,27 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Write this block's partial; returns true in the last block to finish, with
-// the ordered sum of all partials in *total (thread 0).
-__device__ __forceinline__ bool last_block_sum(double v, double* part, unsigned int* counter, double* total) {
+// the ordered sum of all partials in *total (thread 0).  nblocks / bid: the
+// blocks taking part and this block's index among them (the grid, unless
+// several reductions share one launch).
+__device__ __forceinline__ bool last_block_sum(double v, double* part, unsigned int* counter, double* total,
+                                               int nblocks = -1, int bid = -1) {
   __shared__ double sh[32];
   __shared__ bool is_last;
+  if (nblocks < 0) nblocks = (int)gridDim.x;
+  if (bid < 0) bid = (int)blockIdx.x;
   const double b = block_sum(v, sh);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = b;
+    part[bid] = b;
     __threadfence();
     const unsigned int t = atomicAdd(counter, 1u);
-    is_last = (t == gridDim.x - 1);
+    is_last = (t == (unsigned)nblocks - 1);
   }
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
   double s = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(part + i);
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += __ldcg(part + i);
   const double tot = block_sum(s, sh);
   if (threadIdx.x == 0) {
     *total = tot;
@@ -1241,6 +1253,9 @@ struct EngineView {
   int cg_blocks = 1, spmv_blocks = 1;
   i64 sell_real_entries = 0;
   int* ctr = nullptr;              // per-level launch counters (epochs), shared with the single path
+  int dim = 2, device = 0;
+  double* Fbuf = nullptr;          // the engine's staging of F and U (solve order / user order)
+  double* Ubuf = nullptr;
 };
 
 // k independent PCG solves on one hierarchy whose every sweep, transfer and
@@ -1254,6 +1269,21 @@ struct MultiBase {
 };
 template <int D, typename S>
 MultiBase* make_multi(const EngineView<float>& v);
+
+// Several hierarchies advanced together, one right-hand side each: every
+// region level's sweeps, residuals and transfers of all of them in one launch
+// per level and phase, their tails in one launch (a cluster each), and the
+// outer CG kernels of all of them in one launch each (solve_multi.cu).
+// views: the engines' views (same V-cycle precision S, gamma 1, not
+// additive); F[i], U[i]: host or device vectors of hierarchy i.  Each result
+// is the one vasmg_solve gives for that hierarchy alone.  *launches receives
+// the kernels launched.
+template <typename S>
+int batch_solve(const std::vector<EngineView<float>>& views, cudaStream_t stream, const double* const* F,
+                double* const* U, double tol, vasmg_stats* st, i64* launches);
+// CTAs of the batched region sweep that the device holds at once
+template <typename S>
+int batch_sweep_capacity();
 
 
 }  // namespace vasmg

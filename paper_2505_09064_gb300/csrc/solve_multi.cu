@@ -1216,6 +1216,680 @@ struct MultiEngine : MultiBase {
   }
 };
 
+// ------------------------------------------------------------------ several hierarchies per launch
+
+// One hierarchy's region level in a batched launch: its CTAs are
+// [cta0, cta0 + nb) of the grid (nb = its regions for the sweeps, its blocks
+// for the plain kernels).
+struct BatchItem {
+  LV<float> lv;
+  int dim, G, cta0, nb;
+};
+
+__device__ __forceinline__ int batch_item_of(const BatchItem* __restrict__ it, int n, int b) {
+  int i = 0;
+  while (i + 1 < n && it[i + 1].cta0 <= b) ++i;
+  return i;
+}
+
+// Region k's forward sweep from zero (MODE 0) or backward sweep (MODE 1):
+// the steps of vdownm_kernel / vupm_kernel with one right-hand side, the exit
+// counted over this hierarchy's R regions.
+template <int D, typename S, int MODE>
+__device__ __forceinline__ void sweep_region(const LV<float>& L, int k, int G, int R, int* abort_flag) {
+  using V = float;
+  __shared__ unsigned s_epoch;
+  if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + (MODE == 0 ? C_DEPOCH : C_UEPOCH));
+  __syncthreads();
+  const unsigned epoch = s_epoch;
+  const int C = L.ncol;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  const int nb0 = __ldg(L.nb_rp + k), nnb = __ldg(L.nb_rp + k + 1) - nb0;
+  unsigned long long* pg = MODE == 0 ? L.pg_d : L.pg_u;
+  unsigned long long* mine = pg + k;
+  unsigned stage = 0;
+  for (int i = 0; i < C; ++i) {
+    const int c = MODE == 0 ? i : C - 1 - i;
+    const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+    if (r0 < r1) {
+      RowPFM<D, 1, V> cur;
+      rowm_prefetch<D, 1, V, S, MODE>(L, r0 + g, r0 + g < r1, lane, cur);
+      if (stage > 0 && !wait_regions(L.nb + nb0, nnb, pg, epoch, stage, abort_flag)) break;
+      rowsm_pipelined<D, 1, V, S, MODE>(L, r0, r1, G, cur);
+    }
+    publish_stage(mine, epoch, ++stage);
+  }
+  leave(L.ctr, MODE == 0 ? C_DEXIT : C_UEXIT, MODE == 0 ? C_DEPOCH : C_UEPOCH, R);
+}
+
+template <typename S, int MODE>
+__global__ void __launch_bounds__(DFM_THREADS, 2) sweepb_kernel(const BatchItem* __restrict__ items, int nitems,
+                                                               int* abort_flag) {
+  const BatchItem& it = items[batch_item_of(items, nitems, blockIdx.x)];
+  if (it.dim == 2) sweep_region<2, S, MODE>(it.lv, blockIdx.x - it.cta0, it.G, it.nb, abort_flag);
+  else sweep_region<3, S, MODE>(it.lv, blockIdx.x - it.cta0, it.G, it.nb, abort_flag);
+}
+
+template <int D, typename S>
+__device__ __forceinline__ void residual_rows(const LV<float>& L, int lb, int nb, int G) {
+  const int NG = DFM_THREADS / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
+  for (int base = lb * NG; base < L.nv; base += nb * NG) {
+    RowPFM<D, 1, float> st;
+    rowm_prefetch<D, 1, float, S, 2>(L, base + g, base + g < L.nv, lane, st);
+    rowm_finish<D, 1, float, S, 2>(L, base + g, base + g < L.nv, lane, G, st);
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(DFM_THREADS) residualb_kernel(const BatchItem* __restrict__ items, int nitems) {
+  const BatchItem& it = items[batch_item_of(items, nitems, blockIdx.x)];
+  const int lb = blockIdx.x - it.cta0;
+  if (it.dim == 2) residual_rows<2, S>(it.lv, lb, it.nb, it.G);
+  else residual_rows<3, S>(it.lv, lb, it.nb, it.G);
+}
+
+// PHASE 0: b_{l+1} = R r_l, 1: x_l += P x_{l+1}, thread per row
+template <int PHASE>
+__global__ void __launch_bounds__(DFM_THREADS) transferb_kernel(const BatchItem* __restrict__ items, int nitems) {
+  const BatchItem& it = items[batch_item_of(items, nitems, blockIdx.x)];
+  const LV<float>& L = it.lv;
+  const int lb = blockIdx.x - it.cta0, stride = it.nb * blockDim.x;
+  const int n = PHASE == 0 ? L.nvc : L.nv;
+  for (int i = lb * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (PHASE == 0) {
+      if (it.dim == 2) restrictm_row<2, 1, float>(L, i);
+      else restrictm_row<3, 1, float>(L, i);
+    } else {
+      if (it.dim == 2) prolongm_row<2, 1, float>(L, i);
+      else prolongm_row<3, 1, float>(L, i);
+    }
+  }
+}
+
+// Every hierarchy's tail: cluster c runs hierarchy c's levels from its own
+// first tail level down and back.
+template <typename S>
+__global__ void __launch_bounds__(TAIL_THREADS) tailb_kernel(const TailArgs<float>* __restrict__ args,
+                                                             const int* __restrict__ dims) {
+  const int c = blockIdx.x / (int)cluster_size();
+  if (dims[c] == 2) tail_run<2, float, S>(args[c]);
+  else tail_run<3, float, S>(args[c]);
+}
+
+// One hierarchy's outer CG in a batched launch (its own vectors, scalars and
+// partials; its own grid sizes, so its reductions are those of vasmg_solve).
+struct CGB {
+  CGArgs a;
+  float* b0;          // level-0 b of its V-cycle
+  const float* z;     // level-0 x of its V-cycle
+  const double* F;    // user order
+  double* Uout;       // user order
+  int dim, cg_blocks, spmv_blocks;
+};
+
+__global__ void __launch_bounds__(CG_THREADS) cgb_init_kernel(const CGB* __restrict__ items) {
+  const CGB& m = items[blockIdx.y];
+  if ((int)blockIdx.x >= m.cg_blocks) return;
+  const CGArgs& a = m.a;
+  const int D = m.dim;
+  const long long n = (long long)a.nv * D;
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)m.cg_blocks * blockDim.x) {
+    const long long r = t / D;
+    const int c = (int)(t - r * D);
+    const long long g = (long long)__ldg(a.perm + r) * D + c;
+    const double v = __ldg(a.isdir + g) ? 0.0 : m.F[g] - __ldg(a.lift + g);
+    a.r[t] = v;
+    a.U[t] = 0.0;
+    a.p[t] = 0.0;
+    m.b0[t] = (float)v;
+    acc += v * v;
+  }
+  double tot;
+  if (last_block_sum(acc, a.part, &a.sc->cnt[0], &tot, m.cg_blocks, blockIdx.x) && threadIdx.x == 0) {
+    Scalars* s = a.sc;
+    s->res0 = sqrt(tot);
+    s->rr = tot;
+    s->relres = 1.0;
+    s->iter = 0;
+    s->bodies = 0;
+    s->first = 1;
+    s->status = 0;
+    s->abort = 0;
+    s->done = (s->res0 == 0.0) ? 1 : 0;
+    if (s->done) s->relres = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(CG_THREADS) cgb_rz_kernel(const CGB* __restrict__ items) {
+  const CGB& m = items[blockIdx.y];
+  if ((int)blockIdx.x >= m.cg_blocks) return;
+  const CGArgs& a = m.a;
+  Scalars* s = a.sc;
+  if (*(volatile int*)&s->done) return;
+  const long long n = (long long)a.nv * m.dim;
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)m.cg_blocks * blockDim.x)
+    acc += a.r[t] * (double)__ldcg(m.z + t);
+  double tot;
+  if (last_block_sum(acc, a.part, &s->cnt[1], &tot, m.cg_blocks, blockIdx.x) && threadIdx.x == 0) {
+    s->beta = s->first ? 0.0 : tot / s->rho;
+    s->rho = tot;
+    s->first = 0;
+  }
+}
+
+__global__ void __launch_bounds__(CG_THREADS) cgb_pupdate_kernel(const CGB* __restrict__ items) {
+  const CGB& m = items[blockIdx.y];
+  if ((int)blockIdx.x >= m.cg_blocks) return;
+  const CGArgs& a = m.a;
+  if (a.sc->done) return;
+  const double beta = a.sc->beta;
+  const long long n = (long long)a.nv * m.dim;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)m.cg_blocks * blockDim.x)
+    a.p[t] = (double)__ldcg(m.z + t) + beta * a.p[t];
+}
+
+template <int D>
+__device__ __forceinline__ void spmv_rows(const CGB& m) {
+  const CGArgs& a = m.a;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)m.spmv_blocks * blockDim.x) >> 5;
+  const long long nslices = a.sell_n >> 5;
+  double dot = 0.0;
+  for (long long s = warp; s < nslices; s += nwarps) {
+    const long long base = __ldg(a.sell_ptr + s) + lane;
+    const int w = __ldg(a.sell_w + s);
+    const int row = __ldg(a.sell_rows + (s << 5) + lane);
+    double acc[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] = 0.0;
+    for (int k = 0; k < w; ++k) {
+      const long long idx = base + ((long long)k << 5);
+      const int j = __ldg(a.sell_ci + idx);
+      double pj[D];
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb) pj[bb] = a.p[(long long)j * D + bb];
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int bb = 0; bb < D; ++bb)
+          acc[c] = fma(__ldg(a.sell_v + (long long)(c * D + bb) * a.sell_tot + idx), pj[bb], acc[c]);
+    }
+    if (row >= 0) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        a.q[(long long)row * D + c] = acc[c];
+        dot = fma(acc[c], a.p[(long long)row * D + c], dot);
+      }
+    }
+  }
+  double tot;
+  if (last_block_sum(dot, a.part, &a.sc->cnt[2], &tot, m.spmv_blocks, blockIdx.x) && threadIdx.x == 0) {
+    Scalars* s = a.sc;
+    if (!s->done) {
+      s->pq = tot;
+      if (!(tot > 0.0)) {
+        s->status = VASMG_ERR_BREAKDOWN;
+        s->done = 1;
+        s->alpha = 0.0;
+      } else {
+        s->alpha = s->rho / tot;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CG_THREADS) cgb_spmv_kernel(const CGB* __restrict__ items) {
+  const CGB& m = items[blockIdx.y];
+  if ((int)blockIdx.x >= m.spmv_blocks) return;
+  if (m.dim == 2) spmv_rows<2>(m);
+  else spmv_rows<3>(m);
+}
+
+__global__ void __launch_bounds__(CG_THREADS) cgb_update_kernel(const CGB* __restrict__ items,
+                                                                const int* __restrict__ abort_flag) {
+  const CGB& m = items[blockIdx.y];
+  if ((int)blockIdx.x >= m.cg_blocks) return;
+  const CGArgs& a = m.a;
+  Scalars* s = a.sc;
+  if (*(volatile int*)&s->done) return;
+  const double alpha = s->alpha;
+  const long long n = (long long)a.nv * m.dim;
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)m.cg_blocks * blockDim.x) {
+    a.U[t] += alpha * a.p[t];
+    const double rv = a.r[t] - alpha * a.q[t];
+    a.r[t] = rv;
+    m.b0[t] = (float)rv;
+    acc += rv * rv;
+  }
+  double tot;
+  if (last_block_sum(acc, a.part, &s->cnt[3], &tot, m.cg_blocks, blockIdx.x) && threadIdx.x == 0) {
+    s->rr = tot;
+    s->relres = sqrt(tot) / s->res0;
+    s->iter += 1;
+    if (s->iter <= s->max_iters) a.hist[s->iter - 1] = s->relres;
+    if (*(volatile const int*)abort_flag) {
+      s->done = 1;
+      s->status = VASMG_ERR_TIMEOUT;
+    } else if (s->relres < s->tol) {
+      s->done = 1;
+      s->status = VASMG_OK;
+    } else if (!(s->relres == s->relres)) {
+      s->done = 1;
+      s->status = VASMG_ERR_BREAKDOWN;
+    } else if (s->iter >= s->max_iters) {
+      s->done = 1;
+      s->status = VASMG_NOT_CONVERGED;
+    }
+  }
+}
+
+// Another iteration while any hierarchy is still iterating; more than
+// max_iters + 2 bodies end every solve with VASMG_ERR_TIMEOUT.  ctl[0]:
+// bodies run, ctl[1]: any active.
+template <bool COND>
+__global__ void cgb_cond_kernel(const CGB* __restrict__ items, int nitems, int* ctl, int max_iters,
+                                unsigned long long cond, int count) {
+  if (threadIdx.x != 0) return;
+  if (count) ctl[0] += 1;
+  const bool over = ctl[0] > max_iters + 2;
+  int active = 0;
+  for (int i = 0; i < nitems; ++i) {
+    Scalars* s = items[i].a.sc;
+    if (over && !s->done) {
+      s->done = 1;
+      s->status = VASMG_ERR_TIMEOUT;
+    }
+    active |= s->done ? 0 : 1;
+  }
+  if constexpr (COND) {
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, active ? 1u : 0u);
+  }
+  ctl[1] = active;
+}
+
+__global__ void __launch_bounds__(CG_THREADS) cgb_final_kernel(const CGB* __restrict__ items) {
+  const CGB& m = items[blockIdx.y];
+  if ((int)blockIdx.x >= m.cg_blocks) return;
+  const CGArgs& a = m.a;
+  const int D = m.dim;
+  const long long n = (long long)a.nv * D;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)m.cg_blocks * blockDim.x) {
+    const long long r = t / D;
+    const int c = (int)(t - r * D);
+    const long long g = (long long)__ldg(a.perm + r) * D + c;
+    m.Uout[g] = __ldg(a.isdir + g) ? __ldg(a.udir + g) : a.U[t];
+  }
+}
+
+template <typename S>
+int batch_sweep_capacity() {
+  int dev = 0, sms = 0, bd = 0, bu = 0;
+  VASMG_CUDA(cudaGetDevice(&dev));
+  VASMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, sweepb_kernel<S, 0>, DFM_THREADS, 0));
+  VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, sweepb_kernel<S, 1>, DFM_THREADS, 0));
+  return std::min(bd, bu) * sms;
+}
+
+template <typename S>
+struct BatchRun {
+  const std::vector<EngineView<float>>& v;
+  cudaStream_t s;
+  int n = 0, maxlt = 0, nct = 1, sms = 1, max_iters = 1;
+  size_t tail_smem = 0;
+  // device tables
+  std::vector<DevBuf<BatchItem>> sweep_items, plain_items, restrict_items, prolong_items;
+  std::vector<int> sweep_items_n, sweep_ctas, plain_ctas, restrict_ctas, prolong_ctas;
+  DevBuf<TailArgs<float>> targs;
+  DevBuf<int> tdims, ctl, abort_flag;
+  DevBuf<CGB> cg;
+  int cg_grid = 1, spmv_grid = 1;
+  i64 launches = 0;
+  unsigned long long cond = 0;
+
+  BatchRun(const std::vector<EngineView<float>>& views, cudaStream_t stream) : v(views), s(stream) {
+    n = (int)v.size();
+    int dev = 0;
+    VASMG_CUDA(cudaGetDevice(&dev));
+    VASMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (const auto& e : v) {
+      maxlt = std::max(maxlt, e.lt);
+      nct = std::max(nct, e.nct);
+      max_iters = std::max(max_iters, e.max_iters);
+      size_t sm = e.tail_smem;
+      if (e.ta.kd >= 0 && e.ta.kd >= e.ta.ls) sm = (size_t)e.ta.dsoff * sizeof(float) + sizeof(float) * (size_t)e.ta.dld;
+      tail_smem = std::max(tail_smem, sm);
+    }
+    const int cap = batch_sweep_capacity<S>();
+    sweep_items.resize(maxlt);
+    plain_items.resize(maxlt);
+    restrict_items.resize(maxlt);
+    prolong_items.resize(maxlt);
+    sweep_items_n.assign(maxlt, 0);
+    sweep_ctas.assign(maxlt, 0);
+    plain_ctas.assign(maxlt, 0);
+    restrict_ctas.assign(maxlt, 0);
+    prolong_ctas.assign(maxlt, 0);
+    auto blocks_for = [&](i64 threads) { return (int)std::max<i64>(1, std::min<i64>(ceil_div(threads, 256), sms * 8)); };
+    for (int l = 0; l < maxlt; ++l) {
+      std::vector<BatchItem> sw, pl, re, pr;
+      int c0 = 0, p0 = 0, r0 = 0, q0 = 0;
+      for (const auto& e : v) {
+        if (l >= e.lt) continue;
+        BatchItem it{};
+        it.lv = e.lv[l];
+        it.dim = e.dim;
+        it.G = e.G[l];
+        it.cta0 = c0;
+        it.nb = e.lv[l].R;
+        sw.push_back(it);
+        c0 += it.nb;
+        it.cta0 = p0;
+        it.nb = blocks_for((i64)e.lv[l].nv * it.G);
+        pl.push_back(it);
+        p0 += it.nb;
+        it.cta0 = r0;
+        it.nb = blocks_for(e.lv[l].nvc);
+        re.push_back(it);
+        r0 += it.nb;
+        it.cta0 = q0;
+        it.nb = blocks_for(e.lv[l].nv);
+        pr.push_back(it);
+        q0 += it.nb;
+      }
+      VASMG_CHECK(c0 <= cap, VASMG_ERR_UNSUPPORTED, "the batch's regions do not fit the device at once");
+      auto up = [&](DevBuf<BatchItem>& d, const std::vector<BatchItem>& h) {
+        d.alloc((i64)std::max<size_t>(1, h.size()), s);
+        if (!h.empty()) d.upload(h.data(), (i64)h.size());
+      };
+      up(sweep_items[l], sw);
+      up(plain_items[l], pl);
+      up(restrict_items[l], re);
+      up(prolong_items[l], pr);
+      sweep_items_n[l] = (int)sw.size();
+      sweep_ctas[l] = c0;
+      plain_ctas[l] = p0;
+      restrict_ctas[l] = r0;
+      prolong_ctas[l] = q0;
+    }
+    std::vector<TailArgs<float>> ta(n);
+    std::vector<int> dims(n);
+    std::vector<CGB> cgh(n);
+    for (int i = 0; i < n; ++i) {
+      ta[i] = v[i].ta;
+      dims[i] = v[i].dim;
+      CGB& m = cgh[i];
+      m.a = v[i].cga;
+      m.a.cond = 0;
+      m.b0 = v[i].lv[0].b;
+      m.z = v[i].lv[0].x;
+      m.F = v[i].Fbuf;
+      m.Uout = v[i].Ubuf;
+      m.dim = v[i].dim;
+      m.cg_blocks = v[i].cg_blocks;
+      m.spmv_blocks = v[i].spmv_blocks;
+      cg_grid = std::max(cg_grid, m.cg_blocks);
+      spmv_grid = std::max(spmv_grid, m.spmv_blocks);
+    }
+    targs.alloc(n, s);
+    targs.upload(ta.data(), n);
+    tdims.alloc(n, s);
+    tdims.upload(dims.data(), n);
+    cg.alloc(n, s);
+    cg.upload(cgh.data(), n);
+    ctl.alloc(2, s);
+    ctl.zero();
+    abort_flag.alloc(1, s);
+    abort_flag.zero();
+    VASMG_CHECK(tail_smem <= (size_t)TAIL_SMEM_MAX, VASMG_ERR_UNSUPPORTED, "tail levels too large for shared memory");
+    VASMG_CUDA(cudaFuncSetAttribute(tailb_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM_MAX));
+    if (nct > 8 && cudaFuncSetAttribute(tailb_kernel<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                       cudaSuccess)
+      nct = 8;
+    cudaGetLastError();
+    // one cluster size for all tails (a row's arithmetic does not depend on
+    // it): the largest the handles use that the device can hold
+    while (nct > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nct);
+      cfg.blockDim = dim3(TAIL_THREADS);
+      cfg.dynamicSmemBytes = tail_smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = nct;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, tailb_kernel<S>, &cfg) == cudaSuccess && nclusters > 0) break;
+      cudaGetLastError();
+      nct /= 2;
+    }
+  }
+
+  template <typename K>
+  void coop(K kern, int grid, int l) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(DFM_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const BatchItem* items = sweep_items[l].get();
+    const int ni = sweep_items_n[l];
+    int* ab = abort_flag.get();
+    VASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, items, ni, ab));
+    ++launches;
+  }
+  void vcycle() {
+    for (int l = 0; l < maxlt; ++l) {
+      if (!sweep_items_n[l]) continue;
+      coop(sweepb_kernel<S, 0>, sweep_ctas[l], l);
+      residualb_kernel<S><<<plain_ctas[l], DFM_THREADS, 0, s>>>(plain_items[l].get(), sweep_items_n[l]);
+      transferb_kernel<0><<<restrict_ctas[l], DFM_THREADS, 0, s>>>(restrict_items[l].get(), sweep_items_n[l]);
+      launches += 2;
+    }
+    {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nct * n);
+      cfg.blockDim = dim3(TAIL_THREADS);
+      cfg.dynamicSmemBytes = tail_smem;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = nct;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const TailArgs<float>* tp = targs.get();
+      const int* dp = tdims.get();
+      VASMG_CUDA(cudaLaunchKernelEx(&cfg, tailb_kernel<S>, tp, dp));
+      ++launches;
+    }
+    for (int l = maxlt - 1; l >= 0; --l) {
+      if (!sweep_items_n[l]) continue;
+      transferb_kernel<1><<<prolong_ctas[l], DFM_THREADS, 0, s>>>(prolong_items[l].get(), sweep_items_n[l]);
+      ++launches;
+      coop(sweepb_kernel<S, 1>, sweep_ctas[l], l);
+    }
+  }
+  template <bool COND>
+  void body() {
+    vcycle();
+    const dim3 gc(cg_grid, n), gs(spmv_grid, n);
+    cgb_rz_kernel<<<gc, CG_THREADS, 0, s>>>(cg.get());
+    cgb_pupdate_kernel<<<gc, CG_THREADS, 0, s>>>(cg.get());
+    cgb_spmv_kernel<<<gs, CG_THREADS, 0, s>>>(cg.get());
+    cgb_update_kernel<<<gc, CG_THREADS, 0, s>>>(cg.get(), abort_flag.get());
+    cgb_cond_kernel<COND><<<1, 32, 0, s>>>(cg.get(), n, ctl.get(), max_iters, cond, 1);
+    launches += 5;
+  }
+  // init -> WHILE(any active){ body } -> final, as one graph; false if the
+  // conditional graph cannot be built
+  bool run_graph() {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    bool ok = true;
+    cudaGraphConditionalHandle h = 0;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) ok = false;
+    cudaGraph_t out = nullptr;
+    cudaGraphNode_t last = nullptr, wnode = nullptr;
+    if (ok) {
+      cond = (unsigned long long)h;
+      ok = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        cgb_init_kernel<<<dim3(cg_grid, n), CG_THREADS, 0, s>>>(cg.get());
+        cgb_cond_kernel<true><<<1, 32, 0, s>>>(cg.get(), n, ctl.get(), max_iters, cond, 0);
+        ok = cudaStreamEndCapture(s, &out) == cudaSuccess;
+      }
+    }
+    if (ok) {
+      size_t nn = 0;
+      ok = cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn == 2;
+      cudaGraphNode_t nodes[2];
+      if (ok) ok = cudaGraphGetNodes(g, nodes, &nn) == cudaSuccess;
+      if (ok) {
+        cudaKernelNodeParams kp = {};
+        ok = cudaGraphKernelNodeGetParams(nodes[1], &kp) == cudaSuccess;
+        last = (ok && kp.func == (void*)cgb_cond_kernel<true>) ? nodes[1] : nodes[0];
+      }
+    }
+    if (ok) {
+      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      ok = cudaGraphAddNode(&wnode, g, &last, nullptr, 1, &np) == cudaSuccess;
+      if (ok) {
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+          try {
+            body<true>();
+          } catch (...) {
+            ok = false;
+          }
+          ok = (cudaStreamEndCapture(s, &out) == cudaSuccess) && ok;
+        }
+      }
+    }
+    if (ok) {
+      ok = cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        cgb_final_kernel<<<dim3(cg_grid, n), CG_THREADS, 0, s>>>(cg.get());
+        ok = cudaStreamEndCapture(s, &out) == cudaSuccess;
+      }
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+      ex = nullptr;
+      ok = false;
+    }
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    cond = 0;
+    if (!ok) return false;
+    const cudaError_t e = cudaGraphLaunch(ex, s);
+    cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(ex);
+    VASMG_CUDA(e);
+    return true;
+  }
+  // the same with a host loop over per-iteration launches
+  void run_host() {
+    cgb_init_kernel<<<dim3(cg_grid, n), CG_THREADS, 0, s>>>(cg.get());
+    cgb_cond_kernel<false><<<1, 32, 0, s>>>(cg.get(), n, ctl.get(), max_iters, 0, 0);
+    check_launch("cgb_init");
+    int h[2] = {0, 1};
+    VASMG_CUDA(cudaMemcpyAsync(h, ctl.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+    VASMG_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; h[1] && b <= max_iters + 2; ++b) {
+      body<false>();
+      VASMG_CUDA(cudaMemcpyAsync(h, ctl.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+      VASMG_CUDA(cudaStreamSynchronize(s));
+    }
+    cgb_final_kernel<<<dim3(cg_grid, n), CG_THREADS, 0, s>>>(cg.get());
+    check_launch("cgb_final");
+  }
+};
+
+template <typename S>
+int batch_solve(const std::vector<EngineView<float>>& views, cudaStream_t s, const double* const* F,
+                double* const* U, double tol, vasmg_stats* st, i64* launches) {
+  const int n = (int)views.size();
+  if (n == 0) return VASMG_OK;
+  BatchRun<S> br(views, s);
+  for (int i = 0; i < n; ++i) {
+    const EngineView<float>& e = views[i];
+    Scalars init{};
+    init.tol = tol;
+    init.max_iters = e.max_iters;
+    VASMG_CUDA(cudaMemcpyAsync(e.cga.sc, &init, sizeof(Scalars), cudaMemcpyHostToDevice, s));
+    VASMG_CUDA(cudaMemcpyAsync(e.Fbuf, F[i], sizeof(double) * e.nv[0] * e.dim, cudaMemcpyDefault, s));
+  }
+  bool graph = true;
+  for (const auto& e : views) graph = graph && e.use_graph;
+  i64 iter_launches = 0;
+  {
+    // one body's launches, counted by a dry run of the host loop's bookkeeping
+    const i64 before = br.launches;
+    if (!(graph && br.run_graph())) {
+      br.launches = before;
+      br.run_host();
+    }
+    iter_launches = br.launches - before;
+  }
+  std::vector<Scalars> hs(n);
+  int ctlh[2] = {0, 0};
+  for (int i = 0; i < n; ++i)
+    VASMG_CUDA(cudaMemcpyAsync(&hs[i], views[i].cga.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  VASMG_CUDA(cudaMemcpyAsync(ctlh, br.ctl.get(), sizeof(ctlh), cudaMemcpyDeviceToHost, s));
+  int ab = 0;
+  VASMG_CUDA(cudaMemcpyAsync(&ab, br.abort_flag.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  for (int i = 0; i < n; ++i)
+    VASMG_CUDA(cudaMemcpyAsync(U[i], views[i].Ubuf, sizeof(double) * views[i].nv[0] * views[i].dim,
+                               cudaMemcpyDefault, s));
+  VASMG_CUDA(cudaStreamSynchronize(s));
+  // graph path: the body captured once, run ctl[0] times (+ init, condition, final)
+  if (launches) *launches = graph ? 3 + iter_launches * (i64)ctlh[0] : iter_launches + 3;
+  int worst = VASMG_OK;
+  for (int i = 0; i < n; ++i) {
+    int rc = hs[i].status;
+    if (ab) rc = VASMG_ERR_TIMEOUT;
+    if (st) {
+      st[i].iterations = hs[i].iter;
+      st[i].rel_res = hs[i].relres;
+      st[i].n_levels = views[i].L;
+      if (st[i].res_history && st[i].res_history_cap > 0) {
+        const int kk = std::min(st[i].res_history_cap, std::min(hs[i].iter, views[i].max_iters));
+        if (kk > 0)
+          VASMG_CUDA(cudaMemcpy(st[i].res_history, views[i].cga.hist, sizeof(double) * kk, cudaMemcpyDeviceToHost));
+      }
+    }
+    if (rc < 0) worst = std::min(worst, rc);
+    else if (worst >= 0) worst = std::max(worst, rc);
+  }
+  return worst;
+}
+
+template int batch_solve<float>(const std::vector<EngineView<float>>&, cudaStream_t, const double* const*,
+                                double* const*, double, vasmg_stats*, i64*);
+template int batch_solve<__nv_bfloat16>(const std::vector<EngineView<float>>&, cudaStream_t, const double* const*,
+                                        double* const*, double, vasmg_stats*, i64*);
+template int batch_sweep_capacity<float>();
+template int batch_sweep_capacity<__nv_bfloat16>();
+
 template <int D, typename S>
 MultiBase* make_multi(const EngineView<float>& v) {
   return new MultiEngine<D, S>(v);

@@ -247,7 +247,10 @@ def serving_requests(n_req: int, seed: int = 5):
 def serving_run(stream, n_req: int = 32):
     """Continuous-batching server on the serving workload: single-stream
     capacity, Poisson arrivals at 0.5/0.8/0.95 of it, and the plain FP64
-    one-solve-at-a-time path on the same requests."""
+    one-solve-at-a-time path on the same requests.  Each request's slot
+    solves its right-hand sides together (vasmg_solve_multi); the batched
+    executor (one launch per level and phase across requests) is run on the
+    same arrivals beside it."""
     from paper_2505_09064_gb300 import meshgen, vasmg
 
     reqs = serving_requests(n_req)
@@ -266,8 +269,8 @@ def serving_run(stream, n_req: int = 32):
     n_solves = sum(len(F) for F in loads)
     dofs = [prob["coords"].shape[0] * prob["dim"] for prob, _ in reqs]
 
-    def run(slots, precision, rate=None):
-        srv = vasmg.Server(slots=slots, precision=precision)
+    def run(slots, precision, rate=None, batch=False):
+        srv = vasmg.Server(slots=slots, precision=precision, batch=batch)
         rs = meshgen.Stream(77)
         gaps = -np.log(1.0 - rs.uniform(len(reqs))) / rate if rate else np.zeros(len(reqs))
         t0 = time.perf_counter()
@@ -297,10 +300,15 @@ def serving_run(stream, n_req: int = 32):
     loads_out = {}
     for frac in (0.5, 0.8, 0.95):
         loads_out[str(frac)] = run(4, "fp32", rate=frac * cap_rps)
+    # the batched executor: every ready request's next right-hand side in one
+    # round of vasmg_solve_batch (one launch per level and phase for all)
+    batched = {"closed_loop": run(4, "fp32", batch=True), "offered_load": {}}
+    for frac in (0.5, 0.8, 0.95):
+        batched["offered_load"][str(frac)] = run(4, "fp32", rate=frac * cap_rps, batch=True)
     return {"requests": len(reqs), "solves": n_solves, "dofs_min": int(min(dofs)), "dofs_max": int(max(dofs)),
             "slots": 4, "precision": "fp32 V-cycle, fp64 CG",
             "single_stream": single, "closed_loop": closed, "fp64_single_stream": fp64_single,
-            "offered_load": loads_out, "capacity_requests_per_s": cap_rps,
+            "offered_load": loads_out, "batched": batched, "capacity_requests_per_s": cap_rps,
             "recipe": "Poisson arrivals (seed 5/77), mixed 2D/3D jittered P1, 5k-500k dofs log-uniform, "
                       "E~U[1,100], nu~U[0.2,0.45], 1-8 body-force loads each, tol 1e-6"}
 

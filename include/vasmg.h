@@ -242,6 +242,14 @@ typedef struct {
   double tol;                  /* relative residual; default 1e-6 */
   int64_t memory_budget;       /* device bytes for admitted requests; 0: half
                                   the free device memory at creation */
+  int32_t batch;               /* 0 (default): each slot solves its request's
+                                  right-hand sides itself, all of them in one
+                                  vasmg_solve_multi.  1: the slots set up the
+                                  hierarchies, and one executor advances the
+                                  solves of every request ready at the time
+                                  together, one right-hand side of each per
+                                  round, with vasmg_solve_batch (one launch per
+                                  level and phase for all of them) */
 } vasmg_server_opts;
 
 typedef struct {

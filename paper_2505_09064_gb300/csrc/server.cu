@@ -13,6 +13,12 @@
 // overlap on the device; each handle's sweep grids are capped to a share of
 // the device (vasmg_options.max_ctas) so that all running sweeps can be
 // resident together, which their cross-CTA waits require.
+//
+// Batched mode (vasmg_server_opts.batch): a slot sets up its request and hands
+// the hierarchy to one executor thread, which repeatedly takes every request
+// ready at that moment and solves one right-hand side of each with
+// vasmg_solve_batch (one launch per level and phase for all of them); a
+// request with more right-hand sides rejoins the next round.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -66,6 +72,14 @@ int64_t footprint_estimate(int dim, int64_t nv, int64_t ne, int32_t nrhs) {
 }  // namespace
 
 struct vasmg_server {
+  // a request's hierarchy waiting for, or in, a batched round
+  struct Job {
+    vasmg_handle h = nullptr;
+    Request* r = nullptr;
+    size_t next = 0;          // right-hand sides solved so far
+    bool finished = false;
+    int status = VASMG_OK;
+  };
   vasmg_server_opts o{};
   int device = 0;
   int max_ctas = 0;
@@ -77,6 +91,57 @@ struct vasmg_server {
   uint64_t next_id = 1;
   bool stop = false;
   std::vector<std::thread> workers;
+  std::deque<Job*> ready;               // batched mode
+  std::condition_variable cv_ready, cv_solved;
+  bool stop_exec = false;
+  std::thread executor;
+
+  // Batched mode: one right-hand side of every ready request per round.
+  void executor_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+      std::vector<Job*> batch;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_ready.wait(lk, [&] { return !ready.empty() || stop_exec; });
+        if (ready.empty()) break;
+        while (!ready.empty()) {
+          batch.push_back(ready.front());
+          ready.pop_front();
+        }
+      }
+      const int32_t k = (int32_t)batch.size();
+      std::vector<vasmg_handle> hs(k);
+      std::vector<const double*> Fp(k);
+      std::vector<double*> Up(k);
+      std::vector<vasmg_stats> ss(k);
+      for (int32_t i = 0; i < k; ++i) {
+        hs[i] = batch[i]->h;
+        Fp[i] = batch[i]->r->F[batch[i]->next].data();
+        Up[i] = batch[i]->r->U[batch[i]->next];
+      }
+      const int rc = vasmg_solve_batch(k, hs.data(), Fp.data(), Up.data(), o.tol, ss.data());
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int32_t i = 0; i < k; ++i) {
+          Job* j = batch[i];
+          vasmg_request_stats& st = j->r->st;
+          if (rc < 0) {
+            j->status = rc;
+            j->finished = true;
+            continue;
+          }
+          st.iterations += ss[i].iterations;
+          st.max_iterations = std::max(st.max_iterations, ss[i].iterations);
+          st.max_rel_res = std::max(st.max_rel_res, ss[i].rel_res);
+          if (!(ss[i].rel_res < o.tol)) j->status = std::max(j->status, (int)VASMG_NOT_CONVERGED);
+          if (++j->next == j->r->F.size()) j->finished = true;
+          else ready.push_back(j);
+        }
+      }
+      cv_solved.notify_all();
+    }
+  }
 
   void run(Request* r, cudaStream_t stream) {
     vasmg_problem pb{};
@@ -107,7 +172,20 @@ struct vasmg_server {
     int rc = vasmg_setup(&pb, &opt, &h);
     st.setup_ms = now_ms() - t0;
     int worst = rc;
-    if (rc == VASMG_OK) {
+    if (rc == VASMG_OK && o.batch) {
+      const double t1 = now_ms();
+      Job j;
+      j.h = h;
+      j.r = r;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        ready.push_back(&j);
+        cv_ready.notify_all();
+        cv_solved.wait(lk, [&] { return j.finished; });
+      }
+      worst = j.status;
+      st.solve_ms = now_ms() - t1;
+    } else if (rc == VASMG_OK) {
       // every right-hand side of the request in one multi solve: each sweep
       // reads the hierarchy once for all of them, and each result is the one
       // vasmg_solve gives alone
@@ -180,6 +258,7 @@ int vasmg_server_default_opts(vasmg_server_opts* out) {
   out->max_iters = 1000;
   out->tol = 1e-6;
   out->memory_budget = 0;
+  out->batch = 0;
   return VASMG_OK;
 }
 
@@ -189,7 +268,7 @@ int vasmg_server_create(const vasmg_server_opts* opts, vasmg_server** out) {
   vasmg_server_opts o;
   if (opts) o = *opts; else vasmg_server_default_opts(&o);
   if (o.slots <= 0 || o.slots > 64 || !(o.tol > 0.0) || o.max_iters <= 0 || o.memory_budget < 0 ||
-      o.precision < VASMG_FP64 || o.precision > VASMG_FP32_VCYCLE_BF16_SMOOTH)
+      o.precision < VASMG_FP64 || o.precision > VASMG_FP32_VCYCLE_BF16_SMOOTH || o.batch < 0 || o.batch > 1)
     return VASMG_ERR_INVALID_ARG;
   try {
     std::unique_ptr<vasmg_server> s(new vasmg_server());
@@ -202,6 +281,7 @@ int vasmg_server_create(const vasmg_server_opts* opts, vasmg_server** out) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return VASMG_ERR_CUDA;
     s->budget = o.memory_budget > 0 ? o.memory_budget : (int64_t)(free_b / 2);
+    if (o.batch) s->executor = std::thread([p = s.get()] { p->executor_loop(); });
     for (int i = 0; i < o.slots; ++i) s->workers.emplace_back([p = s.get()] { p->worker(); });
     *out = s.release();
     return VASMG_OK;
@@ -289,6 +369,14 @@ int vasmg_server_destroy(vasmg_server* s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
+  if (s->executor.joinable()) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop_exec = true;
+    }
+    s->cv_ready.notify_all();
+    s->executor.join();
+  }
   delete s;
   return VASMG_OK;
 }

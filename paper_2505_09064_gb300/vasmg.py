@@ -56,7 +56,7 @@ class vasmg_options(C.Structure):
 
 class vasmg_server_opts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("precision", C.c_int32), ("max_iters", C.c_int32), ("tol", C.c_double),
-                ("memory_budget", C.c_int64)]
+                ("memory_budget", C.c_int64), ("batch", C.c_int32)]
 
 
 class vasmg_request_stats(C.Structure):
@@ -439,12 +439,13 @@ class Server:
     referenced here until poll() reports the request done."""
 
     def __init__(self, slots: int = 4, precision: str = "fp32", tol: float = 1e-6, max_iters: int = 1000,
-                 memory_budget: int = 0):
+                 memory_budget: int = 0, batch: bool = False):
         lib = load()
         o = vasmg_server_opts()
         _check(lib.vasmg_server_default_opts(C.byref(o)), "vasmg_server_default_opts")
         o.slots, o.precision, o.tol, o.max_iters, o.memory_budget = (slots, PRECISIONS_SERVER[precision], tol,
                                                                       max_iters, memory_budget)
+        o.batch = 1 if batch else 0
         self.s = C.c_void_p()
         _check(lib.vasmg_server_create(C.byref(o), C.byref(self.s)), "vasmg_server_create")
         self._keep = {}

@@ -86,13 +86,18 @@ def test_solve_batch_concurrent_equals_alone(built, precision):
             s.close()
 
 
-def test_server_mix_equals_alone(built):
+@pytest.mark.parametrize("batch", [False, True])
+def test_server_mix_equals_alone(built, batch):
+    """Each request's results equal its solves alone, whether a slot solves
+    its own right-hand sides (together, vasmg_solve_multi) or one executor
+    solves every ready request's next right-hand side in one batched round
+    (vasmg_solve_batch, one launch per level and phase)."""
     probs = [meshgen.make_problem(None, **kw) for kw in MIX]
     nrhs = [1, 3, 2, 1, 2]
     Fss = [_rhs(p, k, 200 + i) for i, (p, k) in enumerate(zip(probs, nrhs))]
     # the server sets its handles up with the lanes per row by rule
     ref = [_alone(p, Fs, "fp32", autotune=False) for p, Fs in zip(probs, Fss)]
-    srv = vasmg.Server(slots=3, precision="fp32")
+    srv = vasmg.Server(slots=3, precision="fp32", batch=batch)
     try:
         tickets, outs = [], []
         for p, Fs in zip(probs, Fss):

@@ -700,8 +700,8 @@ struct Engine : EngineBase {
 
   template <int GG>
   void occ(int* bd, int* bu) {
-    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bd, vdown_kernel<D, GG, V, S>, DF_THREADS, 0));
-    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bu, vup_kernel<D, GG, V, S>, DF_THREADS, 0));
+    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bd, vdown_kernel<D, GG, V, S>, df_threads<D, V>(), 0));
+    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bu, vup_kernel<D, GG, V, S>, df_threads<D, V>(), 0));
   }
   // CTAs of the sweep kernels with g lanes per row that the device holds at once
   i64 sweep_capacity(int g) {
@@ -776,7 +776,7 @@ struct Engine : EngineBase {
   void launch_coop(K kern, int grid, const LV<V>& a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(DF_THREADS);
+    cfg.blockDim = dim3(df_threads<D, V>());
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;

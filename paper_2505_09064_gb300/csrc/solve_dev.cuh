@@ -30,7 +30,13 @@ constexpr int MAX_LEVELS = 40;
 // DENSE_ROWS_PER_CTA^2; the cluster reads M once per V-cycle.
 constexpr int DENSE_ROWS_PER_CTA = 640;
 constexpr int CG_THREADS = 256;
-constexpr int DF_THREADS = 256;
+// Threads of a region CTA of the single-vector sweeps: 1024 (one CTA per SM,
+// 152 larger regions) for 2D levels with FP32 vectors, 256 otherwise.
+// Measured per solve: 2D 1024^2 FP32 57.0 -> 52.8 ms with 1024; the 3D
+// levels (~100 blocks per row) need more than 64 registers per thread and
+// are slower with it (128^3 graded: 555 -> 862 ms).
+template <int D, typename V>
+constexpr int df_threads() { return (D == 2 && sizeof(V) == 4) ? 1024 : 256; }
 constexpr int REGION_MIN_ROWS = 32;  // fewest rows a sweep region is given
 constexpr int SPIN_LIMIT = 1 << 20;   // ~0.1-0.5 s of polling before a wait gives up
 
@@ -530,7 +536,7 @@ __device__ __forceinline__ void leave(int* ctr, int exit_i, int epoch_i, int nct
 // loaded while the current pass gathers x.  `cur` holds the first pass.
 template <int D, int G, typename V, typename S, int MODE>
 __device__ __forceinline__ void rows_pipelined(const LV<V>& L, int r0, int r1, RowPF<D, V>& cur) {
-  constexpr int NG = DF_THREADS / G;
+  constexpr int NG = df_threads<D, V>() / G;
   const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
   for (int base = r0; base < r1; base += NG) {
     const int nb = base + NG;
@@ -552,11 +558,11 @@ __device__ __forceinline__ void rows_pipelined(const LV<V>& L, int r0, int r1, R
 
 // Minimum resident CTAs per SM the kernels are compiled for (register cap).
 template <int D, typename V>
-constexpr int df_min_blocks() { return (D == 2 && sizeof(V) == 4) ? 4 : 2; }
+constexpr int df_min_blocks() { return (D == 2 && sizeof(V) == 4) ? 1 : 2; }
 
 // Forward multicolour sweep from zero (pre-smoothing) of one level.
 template <int D, int G, typename V, typename S>
-__global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
+__global__ void __launch_bounds__(df_threads<D, V>(), df_min_blocks<D, V>())
     vdown_kernel(const __grid_constant__ LV<V> L, Scalars* sc) {
   __shared__ unsigned s_epoch;
   if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_DEPOCH);
@@ -582,7 +588,7 @@ __global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
 
 // Backward multicolour sweep (post-smoothing) of one level.
 template <int D, int G, typename V, typename S>
-__global__ void __launch_bounds__(DF_THREADS, df_min_blocks<D, V>())
+__global__ void __launch_bounds__(df_threads<D, V>(), df_min_blocks<D, V>())
     vup_kernel(const __grid_constant__ LV<V> L, Scalars* sc) {
   __shared__ unsigned s_epoch;
   if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_UEPOCH);

@@ -25,7 +25,7 @@
 
 namespace vasmg {
 
-constexpr int DFM_THREADS = 256;    // threads of the multi sweep CTAs (one CTA per region, as the single sweeps)
+constexpr int DFM_THREADS = 256;    // threads of the batched sweep CTAs and of the plain batched kernels
 constexpr int TAILM_THREADS = 512;  // threads of the multi tail CTAs (more registers per thread than the single tail)
 constexpr int KMAX = 8;             // right-hand sides per pass
 constexpr int KG_SPMV = 4;          // right-hand sides per SpMV launch
@@ -154,7 +154,7 @@ __device__ __forceinline__ void rowm_finish(const L_t& L, int row, bool valid, i
 
 template <int D, int KR, typename V, typename S, int MODE>
 __device__ __forceinline__ void rowsm_pipelined(const LV<V>& L, int r0, int r1, int G, RowPFM<D, KR, V>& cur) {
-  const int NG = DFM_THREADS / G;
+  const int NG = (int)blockDim.x / G;
   const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
   for (int base = r0; base < r1; base += NG) {
     const int nb = base + NG;
@@ -210,13 +210,19 @@ __device__ __forceinline__ void prolongm_row(const L_t& L, int i) {
 
 // ------------------------------------------------------------------ region launches
 
+// The multi sweeps hold as many CTAs per SM as the single sweeps' regions
+// need: 2D levels with FP32 vectors have one 1024-thread region per SM (their
+// multi CTAs take 512 threads, as many as the registers of 8 right-hand
+// sides allow), 3D levels two 256-thread regions.
+template <int D, typename V>
+constexpr int dfm_threads() { return (D == 2 && sizeof(V) == 4) ? 512 : 256; }
 template <int D, typename V>
 constexpr int dfm_min_blocks() { return df_min_blocks<D, V>(); }
 
 // Forward sweep from zero of one region level, KR right-hand sides (the waits
 // and stages of vdown_kernel).
 template <int D, int KR, typename V, typename S>
-__global__ void __launch_bounds__(DFM_THREADS, dfm_min_blocks<D, V>())
+__global__ void __launch_bounds__(dfm_threads<D, V>(), dfm_min_blocks<D, V>())
     vdownm_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int G) {
   __shared__ unsigned s_epoch;
   if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_DEPOCH);
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(DFM_THREADS, dfm_min_blocks<D, V>())
 
 // Backward sweep of one region level, KR right-hand sides.
 template <int D, int KR, typename V, typename S>
-__global__ void __launch_bounds__(DFM_THREADS, dfm_min_blocks<D, V>())
+__global__ void __launch_bounds__(dfm_threads<D, V>(), dfm_min_blocks<D, V>())
     vupm_kernel(const __grid_constant__ LV<V> L, Scalars* sc, int G) {
   __shared__ unsigned s_epoch;
   if (threadIdx.x == 0) s_epoch = *(volatile unsigned*)(L.ctr + C_UEPOCH);
@@ -832,7 +838,7 @@ struct MultiEngine : MultiBase {
   void coop(K kern, int grid, const LV<V>& a, int G, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(DFM_THREADS);
+    cfg.blockDim = dim3(dfm_threads<D, V>());
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -939,8 +945,8 @@ struct MultiEngine : MultiBase {
     // every region of a level must be resident at once: the multi sweep CTAs
     // must fit as many per SM as the single sweeps' regions need
     int bd = 0, bu = 0;
-    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, vdownm_kernel<D, KR, V, S>, DFM_THREADS, 0));
-    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, vupm_kernel<D, KR, V, S>, DFM_THREADS, 0));
+    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, vdownm_kernel<D, KR, V, S>, dfm_threads<D, V>(), 0));
+    VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, vupm_kernel<D, KR, V, S>, dfm_threads<D, V>(), 0));
     for (int l = 0; l < v.lt; ++l)
       VASMG_CHECK((i64)std::min(bd, bu) * v.sms >= v.lv[l].R, VASMG_ERR_UNSUPPORTED,
                   "the multi-right-hand-side sweep cannot hold the level's regions");

@@ -331,6 +331,18 @@ struct Engine : EngineBase {
   // gamma-cycle (gamma >= 2): each level's coarse right-hand side and first
   // coarse correction, kept while the next coarse cycle runs
   std::vector<DevBuf<V>> wb, we;
+  // 3D region levels: the sweeps' operator parts in the staged order
+  // (vstaged_kernel), [0] the forward sweep's lower part, [1] the backward
+  // sweep's whole rows, each built for the level's lanes per row G
+  struct Staged {
+    int G = 0;                  // 0: not built
+    long long nchunks = 0;
+    DevBuf<int32_t> ci, goff, srow;
+    DevBuf<long long> step_chunk;
+    DevBuf<S> v8, v9;
+    StagedOp<S> op{};
+  };
+  std::vector<Staged> stg[2];
 
   explicit Engine(Ctx& ctx) : c(&ctx) { build(); }
   ~Engine() override {
@@ -475,6 +487,8 @@ struct Engine : EngineBase {
           rph_dev[l].get(), cil_dev[l].get(), offl_dev[l].get(), lv[l].nlo, cih_dev[l].get(), offh_dev[l].get(),
           lv[l].nhi);
       check_launch("split_parts");
+      fill_staged(l, 0);
+      fill_staged(l, 1);
     }
     build_dense_level();
     VASMG_CUDA(cudaStreamSynchronize(s));
@@ -614,6 +628,12 @@ struct Engine : EngineBase {
       c->cta_capacity = c->cta_capacity ? std::min<int>(c->cta_capacity, (int)cap) : (int)cap;
     }
     VASMG_CUDA(cudaFuncSetAttribute(tail_kernel<D, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM_MAX));
+    staged_attrs<4>();
+    staged_attrs<8>();
+    staged_attrs<16>();
+    staged_attrs<32>();
+    stg[0].resize(L);
+    stg[1].resize(L);
     if constexpr (std::is_same<V, float>::value)
       VASMG_CUDA(cudaFuncSetAttribute(dense_level_kernel<D, V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       TAIL_SMEM_MAX));
@@ -695,7 +715,144 @@ struct Engine : EngineBase {
       }
     }
     if (c->autotune) autotune_lanes();
+    build_staged_all();
     VASMG_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ---------------------------------------------------------------- staged sweeps (3D)
+  // Level l's staged parts for lanes g: each colour step's rows dealt to the
+  // NG = STG_T / g groups (longest first, to the group with the fewest slots
+  // so far; on the host, from the row pointers), the chunks filled on the device.
+  void build_staged(int l, int g) {
+    if constexpr (D == 3) {
+      cudaStream_t s = c->stream;
+      SolveLevel& sl = c->S[l];
+      const int nv = (int)sl.nv, C = sl.ncol, R = lv[l].R;
+      constexpr int EPT = stg_ept<S>();
+      const int NG = STG_T / g;
+      VASMG_CHECK(nv < STG_NONE, VASMG_ERR_UNSUPPORTED, "level too large for the staged sweep");
+      const std::vector<int> RS = rs_dev[l].download();
+      for (int m = 0; m < 2; ++m) {
+        Staged& st = stg[m][l];
+        if (st.G == g) continue;
+        st.G = 0;
+        std::vector<int> rp((size_t)nv + 1);
+        VASMG_CUDA(cudaMemcpyAsync(rp.data(), m == 0 ? rpl_dev[l].get() : sl.rp.get(), sizeof(int) * (nv + 1),
+                                   cudaMemcpyDeviceToHost, s));
+        VASMG_CUDA(cudaStreamSynchronize(s));
+        std::vector<long long> step_chunk((size_t)C * R + 1, 0);
+        std::vector<int> goff((size_t)C * R * (NG + 1), 0), srow(std::max(nv, 1), 0);
+        std::vector<int> order, load(NG), grp;
+        std::vector<std::vector<int>> lists(NG);
+        for (int col = 0; col < C; ++col)
+          for (int k = 0; k < R; ++k) {
+            const size_t step = (size_t)col * R + k;
+            const int r0 = RS[(size_t)col * (R + 1) + k], r1 = RS[(size_t)col * (R + 1) + k + 1];
+            auto slots = [&](int r) { return std::max(1, (int)ceil_div(rp[r + 1] - rp[r], g)); };
+            order.resize(r1 - r0);
+            for (int r = r0; r < r1; ++r) order[r - r0] = r;
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return slots(a) > slots(b); });
+            std::fill(load.begin(), load.end(), 0);
+            for (auto& v : lists) v.clear();
+            for (int r : order) {
+              const int gi = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+              load[gi] += slots(r);
+              lists[gi].push_back(r);
+            }
+            int pos = r0, mx = 0;
+            for (int gi = 0; gi < NG; ++gi) {
+              goff[step * (NG + 1) + gi] = pos - r0;
+              for (int r : lists[gi]) srow[pos++] = r;
+              mx = std::max(mx, load[gi]);
+            }
+            goff[step * (NG + 1) + NG] = pos - r0;
+            step_chunk[step + 1] = step_chunk[step] + ceil_div(mx, EPT);
+          }
+        const i64 nch = step_chunk[(size_t)C * R];
+        st.step_chunk.alloc((i64)step_chunk.size(), s);
+        st.step_chunk.upload(step_chunk.data(), (i64)step_chunk.size());
+        st.goff.alloc((i64)goff.size(), s);
+        st.goff.upload(goff.data(), (i64)goff.size());
+        st.srow.alloc((i64)srow.size(), s);
+        st.srow.upload(srow.data(), (i64)srow.size());
+        const i64 ne = std::max<i64>(1, nch) * STG_T * EPT;
+        st.ci.alloc(ne, s);
+        st.v8.alloc(ne * 8, s);
+        st.v9.alloc(ne, s);
+        VASMG_CHECK(((uintptr_t)st.ci.get() | (uintptr_t)st.v8.get() | (uintptr_t)st.v9.get()) % 16 == 0,
+                    VASMG_ERR_CUDA, "staged operator not 16-byte aligned");
+        st.nchunks = nch;
+        st.op.ci = st.ci.get();
+        st.op.v8 = st.v8.get();
+        st.op.v9 = st.v9.get();
+        st.op.step_chunk = st.step_chunk.get();
+        st.op.goff = st.goff.get();
+        st.op.srow = st.srow.get();
+        st.G = g;
+        fill_staged(l, m);
+      }
+    } else {
+      (void)l;
+      (void)g;
+    }
+  }
+  // (re)fill level l's staged part m from the level's blocks
+  void fill_staged(int l, int m) {
+    Staged& st = stg[m][l];
+    if (st.G == 0 || st.nchunks == 0) return;
+    SolveLevel& sl = c->S[l];
+    const i64 threads = (i64)sl.ncol * lv[l].R * STG_T;
+    if (m == 0)
+      stage_fill_kernel<S><<<grid_for(threads, 256), 256, 0, c->stream>>>(
+          rpl_dev[l].get(), cil_dev[l].get(), offl_dev[l].get(), nnz_lo[l], lv[l].RS, lv[l].R, sl.ncol,
+          st.step_chunk.get(), st.goff.get(), st.srow.get(), st.G, st.ci.get(), st.v8.get(), st.v9.get());
+    else
+      stage_fill_kernel<S><<<grid_for(threads, 256), 256, 0, c->stream>>>(
+          sl.rp.get(), sl.ci.get(), (const S*)off_ptr(sl), sl.nnz, lv[l].RS, lv[l].R, sl.ncol, st.step_chunk.get(),
+          st.goff.get(), st.srow.get(), st.G, st.ci.get(), st.v8.get(), st.v9.get());
+    check_launch("stage_fill");
+  }
+  bool staged_on(int l) const {
+    return D == 3 && l < lt && stg[0][l].G != 0 && stg[0][l].G == G[l] && stg[1][l].G == G[l];
+  }
+  template <int GG>
+  void occ_staged(int* bd, int* bu) {
+    if constexpr (D == 3) {
+      VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bd, vstaged_kernel<D, GG, V, S, 0>, STG_T + 32,
+                                                               stg_smem_bytes<S>()));
+      VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bu, vstaged_kernel<D, GG, V, S, 1>, STG_T + 32,
+                                                               stg_smem_bytes<S>()));
+    } else {
+      *bd = *bu = 0;
+    }
+  }
+  // CTAs of the staged sweeps with g lanes per row that the device holds at once
+  i64 staged_capacity(int g) {
+    int bd = 0, bu = 0;
+    switch (g) {
+      case 4: occ_staged<4>(&bd, &bu); break;
+      case 8: occ_staged<8>(&bd, &bu); break;
+      case 16: occ_staged<16>(&bd, &bu); break;
+      default: occ_staged<32>(&bd, &bu); break;
+    }
+    return (i64)std::min(bd, bu) * sms_;
+  }
+  template <int GG>
+  void staged_attrs() {
+    if constexpr (D == 3) {
+      VASMG_CUDA(cudaFuncSetAttribute(vstaged_kernel<D, GG, V, S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      stg_smem_bytes<S>()));
+      VASMG_CUDA(cudaFuncSetAttribute(vstaged_kernel<D, GG, V, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      stg_smem_bytes<S>()));
+    }
+  }
+  // the staged copies of every 3D region level for its lanes G, where the
+  // staged kernels can hold the level's region grid
+  void build_staged_all() {
+    if constexpr (D == 3) {
+      for (int l = 0; l < lt; ++l)
+        if (staged_capacity(G[l]) >= lv[l].R) build_staged(l, G[l]);
+    }
   }
 
   template <int GG>
@@ -744,6 +901,7 @@ struct Engine : EngineBase {
       for (int g : {4, 8, 16, 32}) {
         if (sweep_capacity(g) < lv[l].R) continue;
         G[l] = g;
+        if (D == 3 && staged_capacity(g) >= lv[l].R) build_staged(l, g);
         auto run = [&]() {
           down(l, 1, s);
           down(l, 2, s);
@@ -772,6 +930,39 @@ struct Engine : EngineBase {
 
   // ---------------------------------------------------------------- launches
   // cooperative launch: every CTA (region) of the grid is resident at once
+  // cooperative launch of a staged sweep (producer warp, shared-memory ring)
+  template <typename K>
+  void launch_coop_staged(K kern, int grid, const LV<V>& a, const StagedOp<S>& o, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(STG_T + 32);
+    cfg.dynamicSmemBytes = stg_smem_bytes<S>();
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    Scalars* scp = sc.get();
+    VASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, a, o, scp));
+    ++launch_counter;
+  }
+  template <int MODE>
+  void sweep_staged(int l, cudaStream_t s) {
+    if constexpr (D == 3) {
+      const StagedOp<S>& o = stg[MODE][l].op;
+      const int g = lv[l].R;
+      switch (G[l]) {
+        case 4: launch_coop_staged(vstaged_kernel<D, 4, V, S, MODE>, g, lv[l], o, s); break;
+        case 8: launch_coop_staged(vstaged_kernel<D, 8, V, S, MODE>, g, lv[l], o, s); break;
+        case 16: launch_coop_staged(vstaged_kernel<D, 16, V, S, MODE>, g, lv[l], o, s); break;
+        default: launch_coop_staged(vstaged_kernel<D, 32, V, S, MODE>, g, lv[l], o, s); break;
+      }
+    } else {
+      (void)l;
+      (void)s;
+    }
+  }
   template <typename K>
   void launch_coop(K kern, int grid, const LV<V>& a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
@@ -796,7 +987,9 @@ struct Engine : EngineBase {
   // phases: 1 forward sweep (zero start), 2 residual, 4 restriction
   void down(int l, int phases, cudaStream_t s) {
     const int g = lv[l].R;
-    if (phases & 1) {
+    if ((phases & 1) && staged_on(l)) {
+      sweep_staged<0>(l, s);
+    } else if (phases & 1) {
       switch (G[l]) {
         case 4: launch_coop(vdown_kernel<D, 4, V, S>, g, lv[l], s); break;
         case 8: launch_coop(vdown_kernel<D, 8, V, S>, g, lv[l], s); break;
@@ -823,7 +1016,9 @@ struct Engine : EngineBase {
       prolong_kernel<D, V><<<plain_grid(lv[l].nv), 256, 0, s>>>(lv[l]);
       ++launch_counter;
     }
-    if (phases & 2) {
+    if ((phases & 2) && staged_on(l)) {
+      sweep_staged<1>(l, s);
+    } else if (phases & 2) {
       const int g = lv[l].R;
       switch (G[l]) {
         case 4: launch_coop(vup_kernel<D, 4, V, S>, g, lv[l], s); break;

@@ -477,9 +477,19 @@ __device__ __forceinline__ void prolong_row(const L_t& L, int i) {
 
 // ------------------------------------------------------------------ region progress
 
+// Barrier of the NT threads 0..NT-1 of the CTA (named barrier 1), or of the
+// whole CTA when NT is 0.
+template <int NT = 0>
+__device__ __forceinline__ void part_sync() {
+  if constexpr (NT == 0) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
 // Wait until every region in list[0..n) has published stage >= need in this
-// launch (epoch); false (uniform over the CTA) if a wait gave up or the abort
-// flag is up.  Warp 0 polls relaxed loads with back-off, then acquires once.
+// launch (epoch); false (uniform over the threads 0..NT-1, or the CTA) if a
+// wait gave up or the abort flag is up.  Warp 0 polls relaxed loads with
+// back-off, then acquires once.
+template <int NT = 0>
 __device__ __forceinline__ bool wait_regions(const int* __restrict__ list, int n, const unsigned long long* pg,
                                              unsigned epoch, unsigned need, int* abort_flag) {
   __shared__ int s_ok;
@@ -505,15 +515,17 @@ __device__ __forceinline__ bool wait_regions(const int* __restrict__ list, int n
     ok = __all_sync(0xffffffffu, ok);
     if (threadIdx.x == 0) s_ok = ok ? 1 : 0;
   }
-  __syncthreads();
+  part_sync<NT>();
   return s_ok != 0;
 }
 
-// Publish this region's stage once every thread of the CTA has written: the
-// barrier orders the CTA's writes before thread 0's release, and a release
-// is cumulative, so a CTA that acquires the stage sees all of them.
+// Publish this region's stage once every thread of the CTA (or every one of
+// its threads 0..NT-1, the ones that write) has written: the barrier orders
+// their writes before thread 0's release, and a release is cumulative, so a
+// CTA that acquires the stage sees all of them.
+template <int NT = 0>
 __device__ __forceinline__ void publish_stage(unsigned long long* f, unsigned epoch, unsigned stage) {
-  __syncthreads();
+  part_sync<NT>();
   if (threadIdx.x == 0) st_release64(f, ((unsigned long long)epoch << 32) | stage);
 }
 
@@ -633,6 +645,331 @@ __global__ void __launch_bounds__(256) restrict_kernel(const __grid_constant__ L
 template <int D, typename V>
 __global__ void __launch_bounds__(256) prolong_kernel(const __grid_constant__ LV<V> L) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.nv; i += gridDim.x * blockDim.x) prolong_row<D, V>(L, i);
+}
+
+// ------------------------------------------------------------------ staged region sweeps (3D)
+//
+// The region sweeps of 3D levels with the operator part they read streamed
+// through shared memory.  Within one colour step of a region, each group of G
+// lanes takes a list of the step's rows, one row after another; lane e of a
+// group takes the row's entries e, e + G, e + 2G, ... (as row_finish does)
+// and the group sums its lanes by the same shuffle tree.  So each thread runs
+// through a stream of slots, ceil(len / G) (at least one) per row of its
+// group.  Each such level keeps the part a sweep reads (forward: the lower
+// part, backward: whole rows) a second time, in stream order: chunk t of a
+// step holds, for every consumer thread, its slots STG_EPT t ..
+// STG_EPT t + STG_EPT - 1 (the column, flagged on the last slot of a row).
+// The rows are dealt to the groups longest first, each to the group with the
+// fewest slots so far, so the streams of a step end close together and the
+// chunks are nearly full.  A producer warp copies a region's chunks ahead,
+// with bulk asynchronous copies, into a ring of shared-memory stages (an
+// mbarrier per stage counts the bytes in, another counts the consumer warps
+// out).  It needs no neighbour data, so it fills the ring while the rows
+// wait for their neighbours, and the rows' critical path keeps only the
+// gathers of x.  Every row's arithmetic, and its order, is that of
+// row_finish: the results are bitwise those of the unstaged sweep (and so of
+// the multi and batched sweeps).
+
+constexpr int STG_T = 256;  // consumer threads of a staged sweep CTA; one producer warp follows them
+// a slot: column in bits 0..29 (STG_NONE: no entry), STG_END: the row ends
+// with this slot; -1: padding after the thread's stream
+constexpr int STG_NONE = 0x3fffffff;
+constexpr int STG_END = 0x40000000;
+
+// slots per consumer thread and chunk (as many gathers in flight): 4 with
+// BF16 blocks, 2 with FP32, 1 with FP64
+template <typename S>
+constexpr int stg_ept() { return 8 / (int)sizeof(S); }
+// bytes of one chunk: the slots, then block components 0..7, then component 8
+template <typename S>
+constexpr int stg_chunk_bytes() { return STG_T * stg_ept<S>() * (4 + 9 * (int)sizeof(S)); }
+// ring stages: at most 96 KB of shared memory per CTA (two CTAs per SM)
+template <typename S>
+constexpr int stg_stages() { return std::min(8, (96 * 1024) / stg_chunk_bytes<S>()); }
+template <typename S>
+constexpr int stg_smem_bytes() { return stg_stages<S>() * stg_chunk_bytes<S>(); }
+
+template <typename S>
+struct StagedOp {
+  const int* ci;                // [chunks][EPT][STG_T] slots
+  const S* v8;                  // [chunks][EPT][STG_T][8] block components 0..7
+  const S* v9;                  // [chunks][EPT][STG_T] block component 8
+  const long long* step_chunk;  // [ncol R + 1]: chunks of colour c in region k: [step_chunk[c R + k], .. + 1])
+  const int* goff;              // [ncol R][NG + 1]: rows of group g in a step: srow[r0 + goff[g] .. r0 + goff[g + 1])
+  const int* srow;              // [nv]: each step's rows [r0, r1), group by group
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for the phase of the given parity to complete.  Gives up (false)
+// after SPIN_LIMIT polls (after the first 64, 64 ns apart), raising the abort
+// flag, or soon after another wait raised it (read every 256 polls; never
+// when abort_flag is null).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, int* abort_flag) {
+  for (int spins = 0;; ++spins) {
+    if (mbar_test(b, parity)) return true;
+    if (spins >= SPIN_LIMIT) {
+      if (abort_flag) atomicExch(abort_flag, 1);
+      return false;
+    }
+    if (spins >= 64) __nanosleep(64);
+    if (abort_flag && (spins & 255) == 255 && *(volatile int*)abort_flag) return false;
+  }
+}
+// bytes from global src to this CTA's shared dst, counted on mbarrier b
+// (both addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
+}
+
+// Block components of slot `slot` of a chunk in shared memory, converted as ldv8 / ldv do.
+template <typename V, typename S>
+__device__ __forceinline__ void stg_block(const unsigned char* chunk, int slot, V (&a)[9]) {
+  constexpr int NE = STG_T * stg_ept<S>();
+  const S* p8 = reinterpret_cast<const S*>(chunk + NE * 4) + (long long)slot * 8;
+  const S* p9 = reinterpret_cast<const S*>(chunk + NE * (4 + 8 * (int)sizeof(S))) + slot;
+  if constexpr (std::is_same<S, float>::value) {
+    const float4 t0 = reinterpret_cast<const float4*>(p8)[0];
+    const float4 t1 = reinterpret_cast<const float4*>(p8)[1];
+    a[0] = t0.x, a[1] = t0.y, a[2] = t0.z, a[3] = t0.w, a[4] = t1.x, a[5] = t1.y, a[6] = t1.z, a[7] = t1.w;
+    a[8] = *p9;
+  } else if constexpr (std::is_same<S, double>::value) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const double2 t = reinterpret_cast<const double2*>(p8)[h];
+      a[2 * h] = t.x, a[2 * h + 1] = t.y;
+    }
+    a[8] = *p9;
+  } else {
+    const uint4 t = *reinterpret_cast<const uint4*>(p8);
+    const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const __nv_bfloat162 v2 = *reinterpret_cast<const __nv_bfloat162*>(&w[h]);
+      a[2 * h] = __low2float(v2), a[2 * h + 1] = __high2float(v2);
+    }
+    a[8] = __bfloat162float(*p9);
+  }
+}
+
+// The producer: region k's chunks in sweep order into the ring.
+template <typename S, int MODE>
+__device__ __forceinline__ void stg_produce(const StagedOp<S>& O, int k, int R, int C, unsigned long long* full,
+                                            unsigned long long* empty, unsigned char* ring, int* abort_flag) {
+  constexpr int NS = stg_stages<S>(), CB = stg_chunk_bytes<S>(), NE = STG_T * stg_ept<S>();
+  long long q = 0;  // chunks issued
+  bool ok = true;
+  for (int i = 0; i < C && ok; ++i) {
+    const int c = MODE == 0 ? i : C - 1 - i;
+    const long long ch0 = __ldg(O.step_chunk + c * R + k), ch1 = __ldg(O.step_chunk + c * R + k + 1);
+    for (long long ch = ch0; ch < ch1; ++ch, ++q) {
+      const int s = (int)(q % NS);
+      if (q >= NS && !mbar_wait(&empty[s], (unsigned)((q / NS - 1) & 1), abort_flag)) {
+        ok = false;
+        break;
+      }
+      unsigned char* dst = ring + s * CB;
+      mbar_arrive_tx(&full[s], CB);
+      bulk_g2s(dst, O.ci + ch * NE, NE * 4, &full[s]);
+      bulk_g2s(dst + NE * 4, O.v8 + ch * NE * 8, NE * 8 * (int)sizeof(S), &full[s]);
+      bulk_g2s(dst + NE * (4 + 8 * (int)sizeof(S)), O.v9 + ch * NE, NE * (int)sizeof(S), &full[s]);
+    }
+  }
+  // the copies still in flight land before the CTA leaves (after an abort
+  // the consumers stop taking chunks)
+  for (long long j = q > NS ? q - NS : 0; j < q; ++j) mbar_wait(&full[j % NS], (unsigned)((j / NS) & 1), nullptr);
+}
+
+// Diagonal inverse row and b of a row (lanes a < D of its group).
+template <int D, typename V>
+__device__ __forceinline__ void stg_row_data(const LV<V>& L, int row, bool load, int lane, V (&di)[D], V (&bv)[D]) {
+  if (load) {
+#pragma unroll
+    for (int bb = 0; bb < D; ++bb) {
+      di[bb] = __ldg((const V*)L.dinv + (long long)(lane * D + bb) * L.nv + row);
+      bv[bb] = ldx<false>((const V*)L.b + (long long)row * D + bb);
+    }
+  }
+}
+
+// The consumers: region k's rows colour by colour, each group of G lanes
+// through its rows' slots, chunk by chunk from the ring.
+template <int D, int G, typename V, typename S, int MODE>
+__device__ __forceinline__ void stg_consume(const LV<V>& L, const StagedOp<S>& O, int k, int R, int C,
+                                            unsigned epoch, unsigned long long* full, unsigned long long* empty,
+                                            const unsigned char* ring, int* abort_flag) {
+  constexpr int NS = stg_stages<S>(), CB = stg_chunk_bytes<S>(), EPT = stg_ept<S>();
+  constexpr int NG = STG_T / G;
+  const int tid = threadIdx.x, g = tid / G, lane = tid & (G - 1);
+  // the lanes of this group within the warp
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
+  const int nb0 = __ldg(L.nb_rp + k), nnb = __ldg(L.nb_rp + k + 1) - nb0;
+  unsigned long long* pg = MODE == 0 ? L.pg_d : L.pg_u;
+  long long q = 0;  // chunks taken
+  for (int i = 0; i < C; ++i) {
+    const int c = MODE == 0 ? i : C - 1 - i;
+    const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+    if (r0 < r1) {
+      const int step = c * R + k;
+      // this group's rows: srow[j0 .. j1)
+      int j = r0 + __ldg(O.goff + (long long)step * (NG + 1) + g);
+      const int j1 = r0 + __ldg(O.goff + (long long)step * (NG + 1) + g + 1);
+      int row = j < j1 ? __ldg(O.srow + j) : -1;
+      V di[D], bv[D], dn[D], bn[D];
+      stg_row_data<D, V>(L, row, row >= 0 && lane < D, lane, di, bv);
+      int rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
+      stg_row_data<D, V>(L, rown, rown >= 0 && lane < D, lane, dn, bn);
+      if (i > 0 && !wait_regions<STG_T>(L.nb + nb0, nnb, pg, epoch, (unsigned)i, abort_flag)) break;
+      const long long nch = __ldg(O.step_chunk + step + 1) - __ldg(O.step_chunk + step);
+      V acc[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] = V(0);
+      for (long long t = 0; t < nch; ++t, ++q) {
+        const int s = (int)(q % NS);
+        const bool ok = mbar_wait(&full[s], (unsigned)((q / NS) & 1), abort_flag);
+        const unsigned char* chunk = ring + s * CB;
+        int v[EPT];
+        V xj[EPT][D];
+#pragma unroll
+        for (int h = 0; h < EPT; ++h) {
+          v[h] = ok ? reinterpret_cast<const int*>(chunk)[h * STG_T + tid] : -1;
+          const int col = v[h] & STG_NONE;
+          if (v[h] >= 0 && col != STG_NONE)
+            ldx_vertex<D, false, false, true>((const V*)L.x + (long long)col * D, xj[h]);
+        }
+#pragma unroll
+        for (int h = 0; h < EPT; ++h) {
+          if (v[h] < 0) continue;
+          if ((v[h] & STG_NONE) != STG_NONE) {
+            V blk[9];
+            stg_block<V, S>(chunk, h * STG_T + tid, blk);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+              for (int bb = 0; bb < D; ++bb) acc[a] += blk[a * D + bb] * xj[h][bb];
+          }
+          if (v[h] & STG_END) {
+            // the row is done: the group's sum, x_row, the next row
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+              for (int a = 0; a < D; ++a) acc[a] += __shfl_xor_sync(gmask, acc[a], o, G);
+            if (row >= 0 && lane < D) {
+              V sum = V(0);
+#pragma unroll
+              for (int bb = 0; bb < D; ++bb) sum += di[bb] * (bv[bb] - acc[bb]);
+              stx<false>(L.x + (long long)row * D + lane, sum);
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) acc[a] = V(0);
+            ++j;
+            row = rown;
+#pragma unroll
+            for (int bb = 0; bb < D; ++bb) di[bb] = dn[bb], bv[bb] = bn[bb];
+            rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
+            stg_row_data<D, V>(L, rown, rown >= 0 && lane < D, lane, dn, bn);
+          }
+        }
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+      }
+    }
+    publish_stage<STG_T>(pg + k, epoch, (unsigned)(i + 1));
+  }
+}
+
+// Forward sweep from zero (MODE 0, lower part) or backward sweep (MODE 1,
+// whole rows) of a 3D region level with the staged operator: the waits and
+// stages of vdown_kernel / vup_kernel.
+template <int D, int G, typename V, typename S, int MODE>
+__global__ void __launch_bounds__(STG_T + 32, 2)
+    vstaged_kernel(const __grid_constant__ LV<V> L, const __grid_constant__ StagedOp<S> O, Scalars* sc) {
+  static_assert(D == 3, "the staged layout holds 3 x 3 blocks");
+  constexpr int NS = stg_stages<S>();
+  extern __shared__ __align__(128) unsigned char stg_ring[];
+  __shared__ __align__(8) unsigned long long full[NS], empty[NS];
+  __shared__ unsigned s_epoch;
+  if (threadIdx.x == 0) {
+    s_epoch = *(volatile unsigned*)(L.ctr + (MODE == 0 ? C_DEPOCH : C_UEPOCH));
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], STG_T / 32);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const unsigned epoch = s_epoch;
+  const int k = blockIdx.x;
+  int* abort_flag = &sc->abort;
+  if (threadIdx.x >= STG_T) {
+    if (threadIdx.x == STG_T) stg_produce<S, MODE>(O, k, L.R, L.ncol, full, empty, stg_ring, abort_flag);
+  } else {
+    stg_consume<D, G, V, S, MODE>(L, O, k, L.R, L.ncol, epoch, full, empty, stg_ring, abort_flag);
+  }
+  leave(L.ctr, MODE == 0 ? C_DEXIT : C_UEXIT, MODE == 0 ? C_DEPOCH : C_UEPOCH);
+}
+
+// Fills the staged copy of one part (rows rp / columns ci / blocks off with n
+// blocks, layout block_index): one thread per step and consumer thread
+// writes that thread's stream and the padding after it.
+template <typename S>
+__global__ void stage_fill_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const S* __restrict__ off,
+                                  long long n, const int* __restrict__ RS, int R, int C,
+                                  const long long* __restrict__ step_chunk, const int* __restrict__ goff,
+                                  const int* __restrict__ srow, int G, int* __restrict__ sci, S* __restrict__ sv8,
+                                  S* __restrict__ sv9) {
+  constexpr int EPT = stg_ept<S>(), NE = STG_T * EPT;
+  const int NG = STG_T / G;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < (long long)C * R * STG_T;
+       w += (long long)gridDim.x * blockDim.x) {
+    const int step = (int)(w / STG_T), tid = (int)(w - (long long)step * STG_T);
+    const int c = step / R, k = step - c * R;
+    const int g = tid / G, lane = tid % G;
+    const int r0 = RS[c * (R + 1) + k];
+    const long long ch0 = step_chunk[step], nslots = (step_chunk[step + 1] - ch0) * EPT;
+    long long pos = 0;
+    auto put = [&](int v, long long kk) {
+      const long long slot = (ch0 + pos / EPT) * NE + (pos % EPT) * STG_T + tid;
+      sci[slot] = v;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sv8[slot * 8 + q] = kk >= 0 ? off[kk * 8 + q] : S(0.0f);
+      sv9[slot] = kk >= 0 ? off[8 * n + kk] : S(0.0f);
+      ++pos;
+    };
+    for (int j = r0 + goff[(long long)step * (NG + 1) + g]; j < r0 + goff[(long long)step * (NG + 1) + g + 1]; ++j) {
+      const int row = srow[j];
+      const int a0 = rp[row], len = rp[row + 1] - a0;
+      const int steps = len > 0 ? (len + G - 1) / G : 1;
+      for (int t = 0; t < steps; ++t) {
+        const int e = t * G + lane;
+        const int end = t == steps - 1 ? STG_END : 0;
+        if (e < len) put(ci[a0 + e] | end, a0 + e);
+        else put(STG_NONE | end, -1);
+      }
+    }
+    while (pos < nslots) put(-1, -1);
+  }
 }
 
 // ------------------------------------------------------------------ coarsest solve and tail

@@ -314,8 +314,11 @@ enum {
   VASMG_EXPORT_LIFT = 15,        /* f64[n] A u_D of the Dirichlet data */
   VASMG_EXPORT_VOL = 16,         /* f64[n_elements] element measures */
   VASMG_EXPORT_DENSE = 17,       /* i64[2] (k, n_k) of the dense level, (-1, 0) if none (level ignored) */
-  VASMG_EXPORT_LANES = 18        /* i32[n_levels] lanes per row of each level's region sweeps, 0 for the
+  VASMG_EXPORT_LANES = 18,       /* i32[n_levels] lanes per row of each level's region sweeps, 0 for the
                                     levels the tail launch runs (level ignored) */
+  VASMG_EXPORT_STAGED = 19       /* i64[5] the staged copies a 3D region level's sweeps stream (forward slots,
+                                    lower-part blocks, backward slots, whole-row blocks, bytes per slot);
+                                    zeros where the sweeps read the operator in place */
 };
 
 /* Copy an exported array to host buffer buf (NULL: only report the size).

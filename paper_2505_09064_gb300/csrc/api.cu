@@ -486,6 +486,13 @@ int vasmg_export(vasmg_handle h, int32_t what, int32_t level, void* buf, int64_t
       put(g.data(), g.size() * sizeof(int32_t));
       break;
     }
+    case VASMG_EXPORT_STAGED: {
+      VASMG_CHECK(lvl_ok, VASMG_ERR_INVALID_ARG, "level out of range");
+      int64_t v[5];
+      staged_info(c, level, v);
+      put(v, sizeof(v));
+      break;
+    }
     case VASMG_EXPORT_DENSE: {
       int kd = -1, dn = 0;
       dense_level_info(c, &kd, &dn);

@@ -256,6 +256,7 @@ int solve_batch_dev(const std::vector<Ctx*>& cs, const double* const* F, double*
 double time_kernel_multi(Ctx& c, int which, int level, int k, int reps, double* bytes);
 void dense_level_info(Ctx& c, int* kd, int* dn);  // the engine's dense level, (-1, 0) if none
 void lanes_info(Ctx& c, int32_t* g, int n);       // lanes per row of the region levels, 0 elsewhere
+void staged_info(Ctx& c, int level, int64_t* v);  // a level's staged sweep copies (see VASMG_EXPORT_STAGED)
 int probe_wait_timeout(double* elapsed_ms);       // the bounded device wait run out on purpose
 int probe_fp64_rate(double* tflops, double* ms);  // FP64 FMA throughput of the current device
 void destroy_solver_state(Ctx& c);

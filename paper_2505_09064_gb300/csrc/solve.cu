@@ -252,6 +252,9 @@ struct EngineBase {
   virtual void dense_level(int* k, int* n) const = 0;
   // lanes per row of the region levels (levels below the tail), 0 elsewhere
   virtual void lanes(int32_t* g, int n) const = 0;
+  // level l's staged sweep copies: (forward slots, lower-part blocks,
+  // backward slots, whole-row blocks, bytes per slot); zeros if unstaged
+  virtual void staged(int l, int64_t* v) const = 0;
   // k right-hand sides on this hierarchy (solve_multi.cu for the FP32-vector modes)
   virtual int solve_multi(Ctx& c, int k, const double* const* F, double* const* U, double tol, vasmg_stats* st) = 0;
   virtual double time_multi(Ctx& c, int which, int level, int k, int reps, double* bytes) = 0;
@@ -336,9 +339,9 @@ struct Engine : EngineBase {
   // sweep's whole rows, each built for the level's lanes per row G
   struct Staged {
     int G = 0;                  // 0: not built
-    long long nchunks = 0;
-    DevBuf<int32_t> ci, goff, srow;
-    DevBuf<long long> step_chunk;
+    long long nslots = 0;
+    DevBuf<int32_t> ci, goff, srow, step_nact;
+    DevBuf<long long> step_off;
     DevBuf<S> v8, v9;
     StagedOp<S> op{};
   };
@@ -740,7 +743,8 @@ struct Engine : EngineBase {
         VASMG_CUDA(cudaMemcpyAsync(rp.data(), m == 0 ? rpl_dev[l].get() : sl.rp.get(), sizeof(int) * (nv + 1),
                                    cudaMemcpyDeviceToHost, s));
         VASMG_CUDA(cudaStreamSynchronize(s));
-        std::vector<long long> step_chunk((size_t)C * R + 1, 0);
+        std::vector<long long> step_off((size_t)C * R + 1, 0);
+        std::vector<int> step_nact((size_t)C * R, 32);
         std::vector<int> goff((size_t)C * R * (NG + 1), 0), srow(std::max(nv, 1), 0);
         std::vector<int> order, load(NG), grp;
         std::vector<std::vector<int>> lists(NG);
@@ -759,33 +763,41 @@ struct Engine : EngineBase {
               load[gi] += slots(r);
               lists[gi].push_back(r);
             }
-            int pos = r0, mx = 0;
+            // the groups with rows are 0 .. used-1 (rows go to the first least
+            // loaded group); the step's chunks hold their warps only
+            int pos = r0, mx = 0, used = 0;
             for (int gi = 0; gi < NG; ++gi) {
               goff[step * (NG + 1) + gi] = pos - r0;
               for (int r : lists[gi]) srow[pos++] = r;
               mx = std::max(mx, load[gi]);
+              if (!lists[gi].empty()) used = gi + 1;
             }
             goff[step * (NG + 1) + NG] = pos - r0;
-            step_chunk[step + 1] = step_chunk[step] + ceil_div(mx, EPT);
+            const int nact = std::min(STG_T, std::max(32, (int)ceil_div(used * g, 32) * 32));
+            step_nact[step] = nact;
+            step_off[step + 1] = step_off[step] + ceil_div(mx, EPT) * EPT * nact;
           }
-        const i64 nch = step_chunk[(size_t)C * R];
-        st.step_chunk.alloc((i64)step_chunk.size(), s);
-        st.step_chunk.upload(step_chunk.data(), (i64)step_chunk.size());
+        const i64 nslot = step_off[(size_t)C * R];
+        st.step_off.alloc((i64)step_off.size(), s);
+        st.step_off.upload(step_off.data(), (i64)step_off.size());
+        st.step_nact.alloc((i64)step_nact.size(), s);
+        st.step_nact.upload(step_nact.data(), (i64)step_nact.size());
         st.goff.alloc((i64)goff.size(), s);
         st.goff.upload(goff.data(), (i64)goff.size());
         st.srow.alloc((i64)srow.size(), s);
         st.srow.upload(srow.data(), (i64)srow.size());
-        const i64 ne = std::max<i64>(1, nch) * STG_T * EPT;
+        const i64 ne = std::max<i64>(STG_T * EPT, nslot);
         st.ci.alloc(ne, s);
         st.v8.alloc(ne * 8, s);
         st.v9.alloc(ne, s);
         VASMG_CHECK(((uintptr_t)st.ci.get() | (uintptr_t)st.v8.get() | (uintptr_t)st.v9.get()) % 16 == 0,
                     VASMG_ERR_CUDA, "staged operator not 16-byte aligned");
-        st.nchunks = nch;
+        st.nslots = nslot;
         st.op.ci = st.ci.get();
         st.op.v8 = st.v8.get();
         st.op.v9 = st.v9.get();
-        st.op.step_chunk = st.step_chunk.get();
+        st.op.step_off = st.step_off.get();
+        st.op.step_nact = st.step_nact.get();
         st.op.goff = st.goff.get();
         st.op.srow = st.srow.get();
         st.G = g;
@@ -799,17 +811,18 @@ struct Engine : EngineBase {
   // (re)fill level l's staged part m from the level's blocks
   void fill_staged(int l, int m) {
     Staged& st = stg[m][l];
-    if (st.G == 0 || st.nchunks == 0) return;
+    if (st.G == 0 || st.nslots == 0) return;
     SolveLevel& sl = c->S[l];
     const i64 threads = (i64)sl.ncol * lv[l].R * STG_T;
     if (m == 0)
       stage_fill_kernel<S><<<grid_for(threads, 256), 256, 0, c->stream>>>(
           rpl_dev[l].get(), cil_dev[l].get(), offl_dev[l].get(), nnz_lo[l], lv[l].RS, lv[l].R, sl.ncol,
-          st.step_chunk.get(), st.goff.get(), st.srow.get(), st.G, st.ci.get(), st.v8.get(), st.v9.get());
+          st.step_off.get(), st.step_nact.get(), st.goff.get(), st.srow.get(), st.G, st.ci.get(), st.v8.get(),
+          st.v9.get());
     else
       stage_fill_kernel<S><<<grid_for(threads, 256), 256, 0, c->stream>>>(
-          sl.rp.get(), sl.ci.get(), (const S*)off_ptr(sl), sl.nnz, lv[l].RS, lv[l].R, sl.ncol, st.step_chunk.get(),
-          st.goff.get(), st.srow.get(), st.G, st.ci.get(), st.v8.get(), st.v9.get());
+          sl.rp.get(), sl.ci.get(), (const S*)off_ptr(sl), sl.nnz, lv[l].RS, lv[l].R, sl.ncol, st.step_off.get(),
+          st.step_nact.get(), st.goff.get(), st.srow.get(), st.G, st.ci.get(), st.v8.get(), st.v9.get());
     check_launch("stage_fill");
   }
   bool staged_on(int l) const {
@@ -1087,6 +1100,15 @@ struct Engine : EngineBase {
   }
   void lanes(int32_t* g, int n) const override {
     for (int l = 0; l < n; ++l) g[l] = l < lt && l < (int)G.size() ? G[l] : 0;
+  }
+  void staged(int l, int64_t* v) const override {
+    for (int q = 0; q < 5; ++q) v[q] = 0;
+    if (l < 0 || l >= L || !staged_on(l)) return;
+    v[0] = stg[0][l].nslots;
+    v[1] = nnz_lo[l];
+    v[2] = stg[1][l].nslots;
+    v[3] = c->S[l].nnz;
+    v[4] = 4 + 9 * (i64)sizeof(S);
   }
   void build_dense_level() {
     kd = -1;
@@ -1814,6 +1836,11 @@ double time_kernel_multi(Ctx& c, int which, int level, int k, int reps, double* 
 void lanes_info(Ctx& c, int32_t* g, int n) {
   for (int l = 0; l < n; ++l) g[l] = 0;
   if (c.eng) c.eng->lanes(g, n);
+}
+
+void staged_info(Ctx& c, int level, int64_t* v) {
+  for (int q = 0; q < 5; ++q) v[q] = 0;
+  if (c.eng) c.eng->staged(level, v);
 }
 
 // The bounded wait on its own: one CTA waits for a stage word that nothing

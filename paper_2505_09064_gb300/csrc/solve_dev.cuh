@@ -657,8 +657,9 @@ __global__ void __launch_bounds__(256) prolong_kernel(const __grid_constant__ LV
 // through a stream of slots, ceil(len / G) (at least one) per row of its
 // group.  Each such level keeps the part a sweep reads (forward: the lower
 // part, backward: whole rows) a second time, in stream order: chunk t of a
-// step holds, for every consumer thread, its slots STG_EPT t ..
-// STG_EPT t + STG_EPT - 1 (the column, flagged on the last slot of a row).
+// step holds, for each of the step's first nact consumer threads (the warps
+// its rows keep busy), its slots STG_EPT t .. STG_EPT t + STG_EPT - 1 (the
+// column, flagged on the last slot of a row).
 // The rows are dealt to the groups longest first, each to the group with the
 // fewest slots so far, so the streams of a step end close together and the
 // chunks are nearly full.  A producer warp copies a region's chunks ahead,
@@ -680,9 +681,10 @@ constexpr int STG_END = 0x40000000;
 // BF16 blocks, 2 with FP32, 1 with FP64
 template <typename S>
 constexpr int stg_ept() { return 8 / (int)sizeof(S); }
-// bytes of one chunk: the slots, then block components 0..7, then component 8
+// bytes of one chunk of nact threads: the slots, then block components 0..7,
+// then component 8 (a multiple of 16 for any nact that is a multiple of 32)
 template <typename S>
-constexpr int stg_chunk_bytes() { return STG_T * stg_ept<S>() * (4 + 9 * (int)sizeof(S)); }
+constexpr int stg_chunk_bytes(int nact = STG_T) { return nact * stg_ept<S>() * (4 + 9 * (int)sizeof(S)); }
 // ring stages: at most 96 KB of shared memory per CTA (two CTAs per SM)
 template <typename S>
 constexpr int stg_stages() { return std::min(8, (96 * 1024) / stg_chunk_bytes<S>()); }
@@ -691,10 +693,11 @@ constexpr int stg_smem_bytes() { return stg_stages<S>() * stg_chunk_bytes<S>(); 
 
 template <typename S>
 struct StagedOp {
-  const int* ci;                // [chunks][EPT][STG_T] slots
-  const S* v8;                  // [chunks][EPT][STG_T][8] block components 0..7
-  const S* v9;                  // [chunks][EPT][STG_T] block component 8
-  const long long* step_chunk;  // [ncol R + 1]: chunks of colour c in region k: [step_chunk[c R + k], .. + 1])
+  const int* ci;                // per step, per chunk: [EPT][nact] slots
+  const S* v8;                  // [EPT][nact][8] block components 0..7 (same slot order)
+  const S* v9;                  // [EPT][nact] block component 8
+  const long long* step_off;    // [ncol R + 1]: first slot of colour c in region k (step c R + k)
+  const int* step_nact;         // [ncol R]: consumer threads the step's chunks hold (a multiple of 32)
   const int* goff;              // [ncol R][NG + 1]: rows of group g in a step: srow[r0 + goff[g] .. r0 + goff[g + 1])
   const int* srow;              // [nv]: each step's rows [r0, r1), group by group
 };
@@ -743,12 +746,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                : "memory");
 }
 
-// Block components of slot `slot` of a chunk in shared memory, converted as ldv8 / ldv do.
+// Block components of slot `slot` of a chunk of ne slots in shared memory,
+// converted as ldv8 / ldv do.
 template <typename V, typename S>
-__device__ __forceinline__ void stg_block(const unsigned char* chunk, int slot, V (&a)[9]) {
-  constexpr int NE = STG_T * stg_ept<S>();
-  const S* p8 = reinterpret_cast<const S*>(chunk + NE * 4) + (long long)slot * 8;
-  const S* p9 = reinterpret_cast<const S*>(chunk + NE * (4 + 8 * (int)sizeof(S))) + slot;
+__device__ __forceinline__ void stg_block(const unsigned char* chunk, int ne, int slot, V (&a)[9]) {
+  const S* p8 = reinterpret_cast<const S*>(chunk + ne * 4) + slot * 8;
+  const S* p9 = reinterpret_cast<const S*>(chunk + ne * (4 + 8 * (int)sizeof(S))) + slot;
   if constexpr (std::is_same<S, float>::value) {
     const float4 t0 = reinterpret_cast<const float4*>(p8)[0];
     const float4 t1 = reinterpret_cast<const float4*>(p8)[1];
@@ -777,23 +780,24 @@ __device__ __forceinline__ void stg_block(const unsigned char* chunk, int slot, 
 template <typename S, int MODE>
 __device__ __forceinline__ void stg_produce(const StagedOp<S>& O, int k, int R, int C, unsigned long long* full,
                                             unsigned long long* empty, unsigned char* ring, int* abort_flag) {
-  constexpr int NS = stg_stages<S>(), CB = stg_chunk_bytes<S>(), NE = STG_T * stg_ept<S>();
+  constexpr int NS = stg_stages<S>(), CB = stg_chunk_bytes<S>(), EPT = stg_ept<S>();
   long long q = 0;  // chunks issued
   bool ok = true;
   for (int i = 0; i < C && ok; ++i) {
-    const int c = MODE == 0 ? i : C - 1 - i;
-    const long long ch0 = __ldg(O.step_chunk + c * R + k), ch1 = __ldg(O.step_chunk + c * R + k + 1);
-    for (long long ch = ch0; ch < ch1; ++ch, ++q) {
+    const int c = MODE == 0 ? i : C - 1 - i, step = c * R + k;
+    const long long e0 = __ldg(O.step_off + step), e1 = __ldg(O.step_off + step + 1);
+    const int ne = EPT * __ldg(O.step_nact + step);  // slots of one chunk of this step
+    for (long long e = e0; e < e1; e += ne, ++q) {
       const int s = (int)(q % NS);
       if (q >= NS && !mbar_wait(&empty[s], (unsigned)((q / NS - 1) & 1), abort_flag)) {
         ok = false;
         break;
       }
       unsigned char* dst = ring + s * CB;
-      mbar_arrive_tx(&full[s], CB);
-      bulk_g2s(dst, O.ci + ch * NE, NE * 4, &full[s]);
-      bulk_g2s(dst + NE * 4, O.v8 + ch * NE * 8, NE * 8 * (int)sizeof(S), &full[s]);
-      bulk_g2s(dst + NE * (4 + 8 * (int)sizeof(S)), O.v9 + ch * NE, NE * (int)sizeof(S), &full[s]);
+      mbar_arrive_tx(&full[s], (unsigned)(ne * (4 + 9 * (int)sizeof(S))));
+      bulk_g2s(dst, O.ci + e, ne * 4, &full[s]);
+      bulk_g2s(dst + ne * 4, O.v8 + e * 8, ne * 8 * (int)sizeof(S), &full[s]);
+      bulk_g2s(dst + ne * (4 + 8 * (int)sizeof(S)), O.v9 + e, ne * (int)sizeof(S), &full[s]);
     }
   }
   // the copies still in flight land before the CTA leaves (after an abort
@@ -835,13 +839,17 @@ __device__ __forceinline__ void stg_consume(const LV<V>& L, const StagedOp<S>& O
       // this group's rows: srow[j0 .. j1)
       int j = r0 + __ldg(O.goff + (long long)step * (NG + 1) + g);
       const int j1 = r0 + __ldg(O.goff + (long long)step * (NG + 1) + g + 1);
+      // the current row, the next (its diagonal inverse and b in flight) and
+      // the one after (its index in flight)
       int row = j < j1 ? __ldg(O.srow + j) : -1;
+      int rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
+      int rown2 = j + 2 < j1 ? __ldg(O.srow + j + 2) : -1;
       V di[D], bv[D], dn[D], bn[D];
       stg_row_data<D, V>(L, row, row >= 0 && lane < D, lane, di, bv);
-      int rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
       stg_row_data<D, V>(L, rown, rown >= 0 && lane < D, lane, dn, bn);
       if (i > 0 && !wait_regions<STG_T>(L.nb + nb0, nnb, pg, epoch, (unsigned)i, abort_flag)) break;
-      const long long nch = __ldg(O.step_chunk + step + 1) - __ldg(O.step_chunk + step);
+      const int nact = __ldg(O.step_nact + step), ne = EPT * nact;
+      const long long nch = (__ldg(O.step_off + step + 1) - __ldg(O.step_off + step)) / ne;
       V acc[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) acc[a] = V(0);
@@ -853,7 +861,7 @@ __device__ __forceinline__ void stg_consume(const LV<V>& L, const StagedOp<S>& O
         V xj[EPT][D];
 #pragma unroll
         for (int h = 0; h < EPT; ++h) {
-          v[h] = ok ? reinterpret_cast<const int*>(chunk)[h * STG_T + tid] : -1;
+          v[h] = ok && tid < nact ? reinterpret_cast<const int*>(chunk)[h * nact + tid] : -1;
           const int col = v[h] & STG_NONE;
           if (v[h] >= 0 && col != STG_NONE)
             ldx_vertex<D, false, false, true>((const V*)L.x + (long long)col * D, xj[h]);
@@ -863,7 +871,7 @@ __device__ __forceinline__ void stg_consume(const LV<V>& L, const StagedOp<S>& O
           if (v[h] < 0) continue;
           if ((v[h] & STG_NONE) != STG_NONE) {
             V blk[9];
-            stg_block<V, S>(chunk, h * STG_T + tid, blk);
+            stg_block<V, S>(chunk, ne, h * nact + tid, blk);
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -885,10 +893,11 @@ __device__ __forceinline__ void stg_consume(const LV<V>& L, const StagedOp<S>& O
             for (int a = 0; a < D; ++a) acc[a] = V(0);
             ++j;
             row = rown;
+            rown = rown2;
 #pragma unroll
             for (int bb = 0; bb < D; ++bb) di[bb] = dn[bb], bv[bb] = bn[bb];
-            rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
             stg_row_data<D, V>(L, rown, rown >= 0 && lane < D, lane, dn, bn);
+            rown2 = j + 2 < j1 ? __ldg(O.srow + j + 2) : -1;
           }
         }
         __syncwarp();
@@ -936,21 +945,23 @@ __global__ void __launch_bounds__(STG_T + 32, 2)
 template <typename S>
 __global__ void stage_fill_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const S* __restrict__ off,
                                   long long n, const int* __restrict__ RS, int R, int C,
-                                  const long long* __restrict__ step_chunk, const int* __restrict__ goff,
-                                  const int* __restrict__ srow, int G, int* __restrict__ sci, S* __restrict__ sv8,
-                                  S* __restrict__ sv9) {
-  constexpr int EPT = stg_ept<S>(), NE = STG_T * EPT;
+                                  const long long* __restrict__ step_off, const int* __restrict__ step_nact,
+                                  const int* __restrict__ goff, const int* __restrict__ srow, int G,
+                                  int* __restrict__ sci, S* __restrict__ sv8, S* __restrict__ sv9) {
+  constexpr int EPT = stg_ept<S>();
   const int NG = STG_T / G;
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < (long long)C * R * STG_T;
        w += (long long)gridDim.x * blockDim.x) {
     const int step = (int)(w / STG_T), tid = (int)(w - (long long)step * STG_T);
+    const int nact = step_nact[step];
+    if (tid >= nact) continue;  // no rows: the step's chunks leave this thread out
     const int c = step / R, k = step - c * R;
     const int g = tid / G, lane = tid % G;
     const int r0 = RS[c * (R + 1) + k];
-    const long long ch0 = step_chunk[step], nslots = (step_chunk[step + 1] - ch0) * EPT;
+    const long long e0 = step_off[step], nslots = (step_off[step + 1] - e0) / nact;
     long long pos = 0;
     auto put = [&](int v, long long kk) {
-      const long long slot = (ch0 + pos / EPT) * NE + (pos % EPT) * STG_T + tid;
+      const long long slot = e0 + (pos / EPT) * EPT * nact + (pos % EPT) * nact + tid;
       sci[slot] = v;
 #pragma unroll
       for (int q = 0; q < 8; ++q) sv8[slot * 8 + q] = kk >= 0 ? off[kk * 8 + q] : S(0.0f);

@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": VASMG_FP64, "fp32": VASMG_FP32_VCYCLE, "bf16": VASMG_FP32_
 
 (EXPORT_MORTON, EXPORT_LEAF, EXPORT_CELLS, EXPORT_LATTICE, EXPORT_P_RP, EXPORT_P_CI, EXPORT_P_W, EXPORT_A_RP,
  EXPORT_A_CI, EXPORT_A_V, EXPORT_DEAD, EXPORT_COLOUR, EXPORT_DINV, EXPORT_BOX, EXPORT_LIFT, EXPORT_VOL,
- EXPORT_DENSE, EXPORT_LANES) = (0, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18)
+ EXPORT_DENSE, EXPORT_LANES, EXPORT_STAGED) = (0, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19)
 OP_MATVEC, OP_SMOOTH_FWD, OP_SMOOTH_BWD, OP_RESIDUAL, OP_RESTRICT, OP_PROLONG, OP_COARSE, OP_VCYCLE, OP_PRECOND = range(9)
 KERNEL_SPMV64, KERNEL_SWEEP, KERNEL_VCYCLE, KERNEL_DOWN, KERNEL_UP = 0, 1, 2, 3, 4
 KERNEL_FWD_SWEEP, KERNEL_RESIDUAL, KERNEL_RESTRICT, KERNEL_PROLONG, KERNEL_TAIL = 5, 6, 7, 8, 9

@@ -45,10 +45,12 @@ TAIL_NV = 20000         # levels this small run inside the single cluster tail l
 SAMPLE_N = {"cube128_graded": 32, "cube64": 32, "square1024_checker": 192, "square64": 64}
 # DRAM bytes (read + write) of one launch from an ncu capture of the current
 # kernel (profiles/); absent when the kernel changed after the capture.  The
-# 128^3 entry is a capture of the same recipe at 64^3 (323.8 MB against
-# 322.1 MB algorithmic) scaled by the algorithmic bytes of the full launch.
+# 128^3 entry is a one-pass capture (dram__bytes_read.sum + write.sum) of the
+# full-size launch of the staged level-1 backward sweep: 2896.8 + 9.8 MB
+# against 2291.9 MB algorithmic (the staged copy's padding slots and the
+# gathers that miss L2).
 TRAFFIC = {
-    ("cube128_graded", "bwd_sweep_l1"): 2303611630.0,
+    ("cube128_graded", "bwd_sweep_l1"): 2906632704.0,
 }
 TOL = 1e-6
 
@@ -574,6 +576,13 @@ def ours(args):
     levels = [vasmg.vasmg_level_info(s.h, l) for l in range(vasmg.vasmg_num_levels(s.h))]
     lanes = [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)]
     dense = [int(v) for v in s.export(vasmg.EXPORT_DENSE, 0, np.int64)]
+    # slots of the staged backward-sweep copy per block, per region level (0: unstaged)
+    staged_pad = []
+    for l in range(len(lanes)):
+        if lanes[l] == 0:
+            break
+        st = s.export(vasmg.EXPORT_STAGED, l, np.int64)
+        staged_pad.append(round(float(st[2]) / float(st[3]), 3) if st[3] > 0 else 0.0)
     setup_ms = st.setup_ms
     op_cx = st.op_complexity
     # the plain FP64 path on the same workload, with the headline solution's
@@ -619,6 +628,7 @@ def ours(args):
                        "levels": len(levels), "level_vertices": [lv[0] for lv in levels],
                        "level_blocks": [lv[1] for lv in levels], "level_colours": [lv[2] for lv in levels],
                        "op_complexity": op_cx, "lanes_per_row": lanes, "dense_level": dense,
+                       "staged_slots_per_block": staged_pad,
                        "setup_ms": setup_ms, "l2": "operators > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "limiter": "latency" if top.startswith("tail") else "latency/HBM",

@@ -1445,6 +1445,11 @@ struct Engine : EngineBase {
     v.device = c->device;
     v.Fbuf = Fbuf.get();
     v.Ubuf = Ubuf.get();
+    for (int l = 0; l < L; ++l) {
+      const bool on = staged_on(l);
+      v.stg_fwd.push_back(on ? (const void*)&stg[0][l].op : nullptr);
+      v.stg_bwd.push_back(on ? (const void*)&stg[1][l].op : nullptr);
+    }
     return v;
   }
   MultiBase* get_multi() {

@@ -1610,6 +1610,9 @@ struct EngineView {
   int dim = 2, device = 0;
   double* Fbuf = nullptr;          // the engine's staging of F and U (solve order / user order)
   double* Ubuf = nullptr;
+  // per level, the engine's StagedOp<S> of the forward / backward sweep
+  // (3D region levels whose sweeps stream a staged copy), else null
+  std::vector<const void*> stg_fwd, stg_bwd;
 };
 
 // k independent PCG solves on one hierarchy whose every sweep, transfer and

@@ -296,6 +296,135 @@ __global__ void __launch_bounds__(256) prolongm_kernel(const __grid_constant__ L
     prolongm_row<D, KR, V>(L, i);
 }
 
+// ------------------------------------------------------------------ staged region sweeps (3D), KR right-hand sides
+
+// The consumers of vstaged_kernel with KR right-hand sides: the same chunks of
+// the level's staged copy (the producer is stg_produce), each slot applied to
+// the KR interleaved vectors of its column, each right-hand side's sums in the
+// order of rowm_finish.  b of a row is loaded when its group starts the row.
+template <int D, int KR, typename V, typename S, int MODE>
+__device__ __forceinline__ void stgm_consume(const LV<V>& L, const StagedOp<S>& O, int k, int R, int C,
+                                             unsigned epoch, unsigned long long* full, unsigned long long* empty,
+                                             const unsigned char* ring, int* abort_flag, int G) {
+  constexpr int NS = stg_stages<S>(), CB = stg_chunk_bytes<S>(), EPT = stg_ept<S>(), N = KR * D;
+  const int NG = STG_T / G;
+  const int tid = threadIdx.x, g = tid / G, lane = tid & (G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
+  const int nb0 = __ldg(L.nb_rp + k), nnb = __ldg(L.nb_rp + k + 1) - nb0;
+  unsigned long long* pg = MODE == 0 ? L.pg_d : L.pg_u;
+  long long q = 0;  // chunks taken
+  for (int i = 0; i < C; ++i) {
+    const int c = MODE == 0 ? i : C - 1 - i;
+    const int r0 = __ldg(L.RS + c * (R + 1) + k), r1 = __ldg(L.RS + c * (R + 1) + k + 1);
+    if (r0 < r1) {
+      const int step = c * R + k;
+      int j = r0 + __ldg(O.goff + (long long)step * (NG + 1) + g);
+      const int j1 = r0 + __ldg(O.goff + (long long)step * (NG + 1) + g + 1);
+      int row = j < j1 ? __ldg(O.srow + j) : -1;
+      int rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
+      V di[D], bv[N];
+      auto row_data = [&]() {
+        if (row >= 0 && lane < D) {
+#pragma unroll
+          for (int bb = 0; bb < D; ++bb) di[bb] = __ldg((const V*)L.dinv + (long long)(lane * D + bb) * L.nv + row);
+          ld_vec_n<N, false>((const V*)L.b + (long long)row * N, bv);
+        }
+      };
+      row_data();
+      if (i > 0 && !wait_regions<STG_T>(L.nb + nb0, nnb, pg, epoch, (unsigned)i, abort_flag)) break;
+      const int nact = __ldg(O.step_nact + step), ne = EPT * nact;
+      const long long nch = (__ldg(O.step_off + step + 1) - __ldg(O.step_off + step)) / ne;
+      V acc[KR][D];
+#pragma unroll
+      for (int r = 0; r < KR; ++r)
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[r][a] = V(0);
+      for (long long t = 0; t < nch; ++t, ++q) {
+        const int s = (int)(q % NS);
+        const bool ok = mbar_wait(&full[s], (unsigned)((q / NS) & 1), abort_flag);
+        const unsigned char* chunk = ring + s * CB;
+#pragma unroll
+        for (int h = 0; h < EPT; ++h) {
+          const int v = ok && tid < nact ? reinterpret_cast<const int*>(chunk)[h * nact + tid] : -1;
+          if (v < 0) continue;
+          const int col = v & STG_NONE;
+          if (col != STG_NONE) {
+            V xj[N];
+            ld_vec_n<N, true>((const V*)L.x + (long long)col * N, xj);
+            V blk[9];
+            stg_block<V, S>(chunk, ne, h * nact + tid, blk);
+#pragma unroll
+            for (int r = 0; r < KR; ++r)
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int bb = 0; bb < D; ++bb) acc[r][a] += blk[a * D + bb] * xj[r * D + bb];
+          }
+          if (v & STG_END) {
+            // the row is done: the group's sums, x_row of every right-hand side, the next row
+            for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+              for (int r = 0; r < KR; ++r)
+#pragma unroll
+                for (int a = 0; a < D; ++a) acc[r][a] += __shfl_xor_sync(gmask, acc[r][a], o, G);
+            if (row >= 0 && lane < D) {
+#pragma unroll
+              for (int r = 0; r < KR; ++r) {
+                V sum = V(0);
+#pragma unroll
+                for (int bb = 0; bb < D; ++bb) sum += di[bb] * (bv[r * D + bb] - acc[r][bb]);
+                __stcg((V*)L.x + ((long long)row * KR + r) * D + lane, sum);
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < KR; ++r)
+#pragma unroll
+              for (int a = 0; a < D; ++a) acc[r][a] = V(0);
+            ++j;
+            row = rown;
+            rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
+            row_data();
+          }
+        }
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+      }
+    }
+    publish_stage<STG_T>(pg + k, epoch, (unsigned)(i + 1));
+  }
+}
+
+// Forward sweep from zero (MODE 0) or backward sweep (MODE 1) of a 3D region
+// level with KR right-hand sides, reading the level's staged copy (as
+// vstaged_kernel; G lanes per row, a runtime argument).
+template <int D, int KR, typename V, typename S, int MODE>
+__global__ void __launch_bounds__(STG_T + 32, 2)
+    vstagedm_kernel(const __grid_constant__ LV<V> L, const __grid_constant__ StagedOp<S> O, Scalars* sc, int G) {
+  static_assert(D == 3, "the staged layout holds 3 x 3 blocks");
+  constexpr int NS = stg_stages<S>();
+  extern __shared__ __align__(128) unsigned char stgm_ring[];
+  __shared__ __align__(8) unsigned long long full[NS], empty[NS];
+  __shared__ unsigned s_epoch;
+  if (threadIdx.x == 0) {
+    s_epoch = *(volatile unsigned*)(L.ctr + (MODE == 0 ? C_DEPOCH : C_UEPOCH));
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], STG_T / 32);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const unsigned epoch = s_epoch;
+  const int k = blockIdx.x;
+  int* abort_flag = &sc->abort;
+  if (threadIdx.x >= STG_T) {
+    if (threadIdx.x == STG_T) stg_produce<S, MODE>(O, k, L.R, L.ncol, full, empty, stgm_ring, abort_flag);
+  } else {
+    stgm_consume<D, KR, V, S, MODE>(L, O, k, L.R, L.ncol, epoch, full, empty, stgm_ring, abort_flag, G);
+  }
+  leave(L.ctr, MODE == 0 ? C_DEXIT : C_UEXIT, MODE == 0 ? C_DEPOCH : C_UEPOCH);
+}
+
 // ------------------------------------------------------------------ tail
 
 // One multicolour sweep of a tail level on the cluster, KR right-hand sides.
@@ -850,11 +979,71 @@ struct MultiEngine : MultiBase {
     ++launch_counter;
   }
 
+  // The staged sweeps with KR right-hand sides (3D): whether their grids of
+  // R CTAs fit the device (measured once per KR; the shared-memory limit is
+  // raised first).
+  int stg_cap[4] = {-1, -1, -1, -1};
+  template <int KR>
+  bool staged_fits(int R) {
+    if constexpr (D == 3) {
+      int& cap_kr = stg_cap[slot(KR)];
+      if (cap_kr < 0) {
+        const int smem = stg_smem_bytes<S>();
+        VASMG_CUDA(cudaFuncSetAttribute(vstagedm_kernel<D, KR, V, S, 0>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        VASMG_CUDA(cudaFuncSetAttribute(vstagedm_kernel<D, KR, V, S, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int bd = 0, bu = 0;
+        VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, vstagedm_kernel<D, KR, V, S, 0>, STG_T + 32,
+                                                                 smem));
+        VASMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, vstagedm_kernel<D, KR, V, S, 1>, STG_T + 32,
+                                                                 smem));
+        cap_kr = std::min(bd, bu) * v.sms;
+      }
+      return cap_kr >= R;
+    } else {
+      (void)R;
+      return false;
+    }
+  }
+  template <typename K>
+  void coop_staged(K kern, int grid, const LV<V>& a, const void* op, int G, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(STG_T + 32);
+    cfg.dynamicSmemBytes = stg_smem_bytes<S>();
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    Scalars* scp = sc.get();
+    const StagedOp<S> o = *static_cast<const StagedOp<S>*>(op);
+    VASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, a, o, scp, G));
+    ++launch_counter;
+  }
+  // level l's sweep in direction MODE from the staged copy, if it has one that fits
+  template <int KR, int MODE>
+  bool sweep_staged(int l, const LV<V>& a, cudaStream_t s) {
+    if constexpr (D == 3) {
+      const std::vector<const void*>& ops = MODE == 0 ? v.stg_fwd : v.stg_bwd;
+      if (l >= (int)ops.size() || !ops[l] || !staged_fits<KR>(a.R)) return false;
+      coop_staged(vstagedm_kernel<D, KR, V, S, MODE>, a.R, a, ops[l], v.G[l], s);
+      return true;
+    } else {
+      (void)l;
+      (void)a;
+      (void)s;
+      return false;
+    }
+  }
+
   // phases: 1 forward sweep, 2 residual, 4 restriction
   template <int KR>
   void down(int l, int phases, cudaStream_t s) {
     const LV<V> a = lvm(l);
-    if (phases & 1) coop(vdownm_kernel<D, KR, V, S>, a.R, a, v.G[l], s);
+    if ((phases & 1) && !sweep_staged<KR, 0>(l, a, s)) coop(vdownm_kernel<D, KR, V, S>, a.R, a, v.G[l], s);
     if (phases & 2) {
       residualm_kernel<D, KR, V, S><<<plain_grid((i64)a.nv * v.G[l]), 256, 0, s>>>(a, v.G[l]);
       ++launch_counter;
@@ -872,7 +1061,7 @@ struct MultiEngine : MultiBase {
       prolongm_kernel<D, KR, V><<<plain_grid(a.nv), 256, 0, s>>>(a);
       ++launch_counter;
     }
-    if (phases & 2) coop(vupm_kernel<D, KR, V, S>, a.R, a, v.G[l], s);
+    if ((phases & 2) && !sweep_staged<KR, 1>(l, a, s)) coop(vupm_kernel<D, KR, V, S>, a.R, a, v.G[l], s);
   }
   template <int KR>
   size_t tail_smem_bytes() const {

@@ -581,8 +581,8 @@ def ours(args):
     for l in range(len(lanes)):
         if lanes[l] == 0:
             break
-        st = s.export(vasmg.EXPORT_STAGED, l, np.int64)
-        staged_pad.append(round(float(st[2]) / float(st[3]), 3) if st[3] > 0 else 0.0)
+        sx = s.export(vasmg.EXPORT_STAGED, l, np.int64)
+        staged_pad.append(round(float(sx[2]) / float(sx[3]), 3) if sx[3] > 0 else 0.0)
     setup_ms = st.setup_ms
     op_cx = st.op_complexity
     # the plain FP64 path on the same workload, with the headline solution's

@@ -171,10 +171,9 @@ __device__ __forceinline__ void ldx_vertex(const V* p, V (&v)[D]) {
   }
 }
 
-__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
@@ -487,8 +486,12 @@ __device__ __forceinline__ void part_sync() {
 
 // Wait until every region in list[0..n) has published stage >= need in this
 // launch (epoch); false (uniform over the threads 0..NT-1, or the CTA) if a
-// wait gave up or the abort flag is up.  Warp 0 polls relaxed loads with
-// back-off, then acquires once.
+// wait gave up or the abort flag is up.  Warp 0 polls, one neighbour per
+// lane, with GPU-scope acquire loads and back-off.  The acquire that sees a
+// neighbour's stage synchronises with that neighbour's release, and the
+// barrier after the polls orders it before every thread's reads.  (A full
+// fence.acq_rel.gpu after relaxed polls also waits for warp 0's own earlier
+// stores to land: the region kernels took 4.7 % longer with it.)
 template <int NT = 0>
 __device__ __forceinline__ bool wait_regions(const int* __restrict__ list, int n, const unsigned long long* pg,
                                              unsigned epoch, unsigned need, int* abort_flag) {
@@ -500,7 +503,7 @@ __device__ __forceinline__ bool wait_regions(const int* __restrict__ list, int n
       int spins = 0;
       unsigned ns = 32;
       for (;;) {
-        const unsigned long long v = ld_relaxed64(f);
+        const unsigned long long v = ld_acquire64(f);
         if ((unsigned)(v >> 32) == epoch && (unsigned)v >= need) break;
         if (++spins > SPIN_LIMIT || *(volatile int*)abort_flag) {
           atomicExch(abort_flag, 1);
@@ -511,7 +514,6 @@ __device__ __forceinline__ bool wait_regions(const int* __restrict__ list, int n
         ns = ns < 256 ? 2 * ns : 256;
       }
     }
-    fence_acq_rel();
     ok = __all_sync(0xffffffffu, ok);
     if (threadIdx.x == 0) s_ok = ok ? 1 : 0;
   }

@@ -382,16 +382,18 @@ def multi_rhs_run(s, F, n, nfree, k, dev, peaks):
     ms_multi = ev0.elapsed_time(ev1)
     launches_multi = vasmg.vasmg_last_launch_count(s.h)
     its = [st.iterations for st in sts]
-    U1 = torch.zeros_like(F)
+    U1s = [torch.zeros_like(F) for _ in range(k)]
+    single_its = []
+    torch.cuda.synchronize()
     ev0.record()
-    single_its, bitwise = [], True
     for i in range(k):
-        rc1, st1, _ = s.solve(Fs[i], U1, TOL)
+        rc1, st1, _ = s.solve(Fs[i], U1s[i], TOL)
         single_its.append(st1.iterations)
-        bitwise = bitwise and bool(torch.equal(U1, Us[i]))
     ev1.record()
     torch.cuda.synchronize()
     ms_single = ev0.elapsed_time(ev1)
+    bitwise = all(bool(torch.equal(U1s[i], Us[i])) for i in range(k))
+    del U1s
     work = float(nfree * sum(its))
     out = {"k": k, "value": work / (ms_multi / 1e3) / 1e6, "unit": "MDOF*iter/s", "ms": ms_multi,
            "solves_per_s": k / (ms_multi / 1e3), "iterations": its, "gpu_launches": launches_multi,

@@ -440,7 +440,27 @@ __device__ __forceinline__ void restrict_row(const L_t& L, int I) {
   V acc[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) acc[a] = V(0);
-  for (int t = __ldg(L.rrp + I); t < __ldg(L.rrp + I + 1); ++t) {
+  // four entries' indices, weights and gathers in flight at a time; the sums
+  // in entry order (the multi and batched restrictions add in the same order)
+  const int t0 = __ldg(L.rrp + I), t1 = __ldg(L.rrp + I + 1);
+  int t = t0;
+  for (; t + 4 <= t1; t += 4) {
+    int ii[4];
+    V ww[4], rr[4][D];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ii[u] = __ldg(L.rci + t + u);
+      ww[u] = __ldg((const V*)L.rw + t + u);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      ldx_vertex<D, LC, true, gather_l1<L_t, LC>()>((const V*)L.r + (long long)ii[u] * D, rr[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] += ww[u] * rr[u][a];
+  }
+  for (; t < t1; ++t) {
     const int i = __ldg(L.rci + t);
     const V w = __ldg((const V*)L.rw + t);
     V ri[D];
@@ -457,7 +477,26 @@ __device__ __forceinline__ void prolong_row(const L_t& L, int i) {
   V acc[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) acc[a] = V(0);
-  for (int t = __ldg(L.prp + i); t < __ldg(L.prp + i + 1); ++t) {
+  // four entries in flight at a time, the sums in entry order (as restrict_row)
+  const int t0 = __ldg(L.prp + i), t1 = __ldg(L.prp + i + 1);
+  int t = t0;
+  for (; t + 4 <= t1; t += 4) {
+    int jj[4];
+    V ww[4], xx[4][D];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      jj[u] = __ldg(L.pci + t + u);
+      ww[u] = __ldg((const V*)L.pw + t + u);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      ldx_vertex<D, LC, true, gather_l1<L_t, LC>()>((const V*)L.xc + (long long)jj[u] * D, xx[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] += ww[u] * xx[u][a];
+  }
+  for (; t < t1; ++t) {
     const int J = __ldg(L.pci + t);
     const V w = __ldg((const V*)L.pw + t);
     V xJ[D];
@@ -629,12 +668,65 @@ __global__ void __launch_bounds__(df_threads<D, V>(), df_min_blocks<D, V>())
 
 // r = -(upper part) x after the zero-start forward sweep: a plain SpMV of
 // the later-colour blocks, G lanes per row, grid-strided over the rows.
+// The residual of one row of a region level (row_pass, MODE 2) with each lane's
+// entries taken two at a time: both blocks and both gathers in flight before
+// the products, which are added in entry order.  The kernel keeps 32 registers
+// with FP32 vectors (8 CTAs per SM): 128^3 graded, level-1 residual
+// 312 -> 291 us.
 template <int D, int G, typename V, typename S>
-__global__ void __launch_bounds__(256) residual_kernel(const __grid_constant__ LV<V> L) {
+__device__ __forceinline__ void residual_row_u2(const LV<V>& L, int row, bool valid, int lane) {
+  RowSeg sg{0, 0, 0, 0};
+  if (valid) sg = seg_range<2>(L, row);
+  V acc[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) acc[a] = V(0);
+  const int* ciA;
+  const S* offA;
+  long long nA;
+  const int* ciB;
+  const S* offB;
+  long long nB;
+  seg_ptrs<2, S>(L, ciA, offA, nA, ciB, offB, nB);
+  int e = lane;
+  for (; e + G < sg.len; e += 2 * G) {
+    V b0[D * D], b1[D * D];
+    const int j0 = seg_entry<D, V, S>(sg, e, ciA, offA, nA, ciB, offB, nB, b0);
+    const int j1 = seg_entry<D, V, S>(sg, e + G, ciA, offA, nA, ciB, offB, nB, b1);
+    V x0[D], x1[D];
+    ldx_vertex<D, false, true, true>((const V*)L.x + (long long)j0 * D, x0);
+    ldx_vertex<D, false, true, true>((const V*)L.x + (long long)j1 * D, x1);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb) acc[a] += b0[a * D + bb] * x0[bb];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb) acc[a] += b1[a * D + bb] * x1[bb];
+  }
+  if (e < sg.len) {
+    V b0[D * D];
+    const int j0 = seg_entry<D, V, S>(sg, e, ciA, offA, nA, ciB, offB, nB, b0);
+    V x0[D];
+    ldx_vertex<D, false, true, true>((const V*)L.x + (long long)j0 * D, x0);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb) acc[a] += b0[a * D + bb] * x0[bb];
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o, G);
+  if (!valid || lane >= D) return;
+  stx<false>(L.r + (long long)row * D + lane, -pick<D>(acc, lane));
+}
+template <int D, int G, typename V, typename S>
+__global__ void __launch_bounds__(256, sizeof(V) == 8 ? 6 : 8) residual_kernel(const __grid_constant__ LV<V> L) {
   constexpr int NG = 256 / G;
   const int g = threadIdx.x / G, lane = threadIdx.x & (G - 1);
   for (int base = blockIdx.x * NG; base < L.nv; base += gridDim.x * NG)
-    row_pass<D, G, V, S, 2>(L, base + g, base + g < L.nv, lane);
+    residual_row_u2<D, G, V, S>(L, base + g, base + g < L.nv, lane);
 }
 
 // b_{l+1} = R r_l (one thread per coarse row)

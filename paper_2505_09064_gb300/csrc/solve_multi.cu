@@ -343,6 +343,9 @@ __device__ __forceinline__ void stgm_consume(const LV<V>& L, const StagedOp<S>& 
         const int s = (int)(q % NS);
         const bool ok = mbar_wait(&full[s], (unsigned)((q / NS) & 1), abort_flag);
         const unsigned char* chunk = ring + s * CB;
+        // up to 4 right-hand sides, two slots at a time with their gathers in
+        // flight together; 8 right-hand sides one slot at a time (registers)
+        if constexpr (KR > 4) {
 #pragma unroll
         for (int h = 0; h < EPT; ++h) {
           const int v = ok && tid < nact ? reinterpret_cast<const int*>(chunk)[h * nact + tid] : -1;
@@ -385,6 +388,61 @@ __device__ __forceinline__ void stgm_consume(const LV<V>& L, const StagedOp<S>& 
             rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
             row_data();
           }
+        }
+        } else {
+        constexpr int PK = 2;
+#pragma unroll
+        for (int h0 = 0; h0 < EPT; h0 += PK) {
+          int vv[PK];
+          V xj[PK][N];
+#pragma unroll
+          for (int u = 0; u < PK; ++u) {
+            vv[u] = ok && tid < nact ? reinterpret_cast<const int*>(chunk)[(h0 + u) * nact + tid] : -1;
+            const int col = vv[u] & STG_NONE;
+            if (vv[u] >= 0 && col != STG_NONE) ld_vec_n<N, true>((const V*)L.x + (long long)col * N, xj[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < PK; ++u) {
+          const int v = vv[u], h = h0 + u;
+          if (v < 0) continue;
+          const int col = v & STG_NONE;
+          if (col != STG_NONE) {
+            V blk[9];
+            stg_block<V, S>(chunk, ne, h * nact + tid, blk);
+#pragma unroll
+            for (int r = 0; r < KR; ++r)
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int bb = 0; bb < D; ++bb) acc[r][a] += blk[a * D + bb] * xj[u][r * D + bb];
+          }
+          if (v & STG_END) {
+            // the row is done: the group's sums, x_row of every right-hand side, the next row
+            for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+              for (int r = 0; r < KR; ++r)
+#pragma unroll
+                for (int a = 0; a < D; ++a) acc[r][a] += __shfl_xor_sync(gmask, acc[r][a], o, G);
+            if (row >= 0 && lane < D) {
+#pragma unroll
+              for (int r = 0; r < KR; ++r) {
+                V sum = V(0);
+#pragma unroll
+                for (int bb = 0; bb < D; ++bb) sum += di[bb] * (bv[r * D + bb] - acc[r][bb]);
+                __stcg((V*)L.x + ((long long)row * KR + r) * D + lane, sum);
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < KR; ++r)
+#pragma unroll
+              for (int a = 0; a < D; ++a) acc[r][a] = V(0);
+            ++j;
+            row = rown;
+            rown = j + 1 < j1 ? __ldg(O.srow + j + 1) : -1;
+            row_data();
+          }
+          }
+        }
         }
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[s]);

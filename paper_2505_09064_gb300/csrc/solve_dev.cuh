@@ -951,7 +951,9 @@ __device__ __forceinline__ void stg_consume(const LV<V>& L, const StagedOp<S>& O
       for (int a = 0; a < D; ++a) acc[a] = V(0);
       for (long long t = 0; t < nch; ++t, ++q) {
         const int s = (int)(q % NS);
-        const bool ok = mbar_wait(&full[s], (unsigned)((q / NS) & 1), abort_flag);
+        // a wait that gave up leaves the chunk unread by the whole warp, so a
+        // lane group never splits between taking and skipping it
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((q / NS) & 1), abort_flag));
         const unsigned char* chunk = ring + s * CB;
         int v[EPT];
         V xj[EPT][D];

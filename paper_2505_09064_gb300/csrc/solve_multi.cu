@@ -341,7 +341,8 @@ __device__ __forceinline__ void stgm_consume(const LV<V>& L, const StagedOp<S>& 
         for (int a = 0; a < D; ++a) acc[r][a] = V(0);
       for (long long t = 0; t < nch; ++t, ++q) {
         const int s = (int)(q % NS);
-        const bool ok = mbar_wait(&full[s], (unsigned)((q / NS) & 1), abort_flag);
+        // warp-uniform: a lane group never splits between taking and skipping a chunk
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((q / NS) & 1), abort_flag));
         const unsigned char* chunk = ring + s * CB;
         // up to 4 right-hand sides, two slots at a time with their gathers in
         // flight together; 8 right-hand sides one slot at a time (registers)

@@ -752,8 +752,8 @@ __global__ void __launch_bounds__(256) prolong_kernel(const __grid_constant__ LV
 // group.  Each such level keeps the part a sweep reads (forward: the lower
 // part, backward: whole rows) a second time, in stream order: chunk t of a
 // step holds, for each of the step's first nact consumer threads (the warps
-// its rows keep busy), its slots STG_EPT t .. STG_EPT t + STG_EPT - 1 (the
-// column, flagged on the last slot of a row).
+// its rows keep busy), its slots EPT t .. EPT t + EPT - 1 (EPT = stg_ept:
+// the column, flagged on the last slot of a row, and the block).
 // The rows are dealt to the groups longest first, each to the group with the
 // fewest slots so far, so the streams of a step end close together and the
 // chunks are nearly full.  A producer warp copies a region's chunks ahead,

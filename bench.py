@@ -78,6 +78,9 @@ def parse():
                     help="KIND:LEVEL (KIND in spmv64, sweep, fwd_sweep, residual, restrict, prolong, tail): set "
                          "up the workload, then launch that kernel once between cudaProfilerStart/Stop (for "
                          "ncu --profile-from-start off) and print its CUDA-event time")
+    ap.add_argument("--profile-k", type=int, default=1,
+                    help="with --profile-kernel: launch the kernel with this many right-hand sides (2, 4 or 8; "
+                         "vasmg_time_kernel_multi, FP32-vector precisions)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="lanes per row by rule (setup then launches no timing runs; for launch-indexed profiles)")
@@ -493,12 +496,15 @@ def ours(args):
         s, F, U, n, nfree = make(args.workload, args.precision)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        kms, kbytes = vasmg.vasmg_time_kernel(s.h, which, int(level), 1)
+        if args.profile_k > 1:
+            kms, kbytes = vasmg.vasmg_time_kernel_multi(s.h, which, int(level), args.profile_k, 1)
+        else:
+            kms, kbytes = vasmg.vasmg_time_kernel(s.h, which, int(level), 1)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         if rank == 0:
-            print(json.dumps({"profile_kernel": args.profile_kernel, "workload": args.workload, "side": args.side,
-                              "precision": args.precision, "ms": kms, "algorithmic_bytes": kbytes,
+            print(json.dumps({"profile_kernel": args.profile_kernel, "k": args.profile_k, "workload": args.workload,
+                              "side": args.side, "precision": args.precision, "ms": kms, "algorithmic_bytes": kbytes,
                               "lanes_per_row": [int(g) for g in s.export(vasmg.EXPORT_LANES, 0, np.int32)],
                               "level_vertices": [vasmg.vasmg_level_info(s.h, l)[0]
                                                  for l in range(vasmg.vasmg_num_levels(s.h))]}), flush=True)

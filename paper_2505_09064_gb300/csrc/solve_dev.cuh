@@ -842,6 +842,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                : "memory");
 }
 
+// The same with an L2 cache policy (createpolicy), e.g. evict-first for a
+// stream read once so that the vectors gathered beside it stay in L2.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsigned bytes, unsigned long long* b,
+                                              unsigned long long policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 // Block components of slot `slot` of a chunk of ne slots in shared memory,
 // converted as ldv8 / ldv do.
 template <typename V, typename S>
@@ -872,11 +888,15 @@ __device__ __forceinline__ void stg_block(const unsigned char* chunk, int ne, in
   }
 }
 
-// The producer: region k's chunks in sweep order into the ring.
-template <typename S, int MODE>
+// The producer: region k's chunks in sweep order into the ring.  EVICT_FIRST:
+// the copies mark the operator stream evict-first in L2 (the multi-RHS
+// sweeps, whose gathered vectors are KR times larger).
+template <typename S, int MODE, bool EVICT_FIRST = false>
 __device__ __forceinline__ void stg_produce(const StagedOp<S>& O, int k, int R, int C, unsigned long long* full,
                                             unsigned long long* empty, unsigned char* ring, int* abort_flag) {
   constexpr int NS = stg_stages<S>(), CB = stg_chunk_bytes<S>(), EPT = stg_ept<S>();
+  unsigned long long pol = 0;
+  if constexpr (EVICT_FIRST) pol = l2_evict_first_policy();
   long long q = 0;  // chunks issued
   bool ok = true;
   for (int i = 0; i < C && ok; ++i) {
@@ -891,9 +911,15 @@ __device__ __forceinline__ void stg_produce(const StagedOp<S>& O, int k, int R, 
       }
       unsigned char* dst = ring + s * CB;
       mbar_arrive_tx(&full[s], (unsigned)(ne * (4 + 9 * (int)sizeof(S))));
-      bulk_g2s(dst, O.ci + e, ne * 4, &full[s]);
-      bulk_g2s(dst + ne * 4, O.v8 + e * 8, ne * 8 * (int)sizeof(S), &full[s]);
-      bulk_g2s(dst + ne * (4 + 8 * (int)sizeof(S)), O.v9 + e, ne * (int)sizeof(S), &full[s]);
+      if constexpr (EVICT_FIRST) {
+        bulk_g2s_hint(dst, O.ci + e, ne * 4, &full[s], pol);
+        bulk_g2s_hint(dst + ne * 4, O.v8 + e * 8, ne * 8 * (int)sizeof(S), &full[s], pol);
+        bulk_g2s_hint(dst + ne * (4 + 8 * (int)sizeof(S)), O.v9 + e, ne * (int)sizeof(S), &full[s], pol);
+      } else {
+        bulk_g2s(dst, O.ci + e, ne * 4, &full[s]);
+        bulk_g2s(dst + ne * 4, O.v8 + e * 8, ne * 8 * (int)sizeof(S), &full[s]);
+        bulk_g2s(dst + ne * (4 + 8 * (int)sizeof(S)), O.v9 + e, ne * (int)sizeof(S), &full[s]);
+      }
     }
   }
   // the copies still in flight land before the CTA leaves (after an abort

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(STG_T + 32, 2)
   const int k = blockIdx.x;
   int* abort_flag = &sc->abort;
   if (threadIdx.x >= STG_T) {
-    if (threadIdx.x == STG_T) stg_produce<S, MODE>(O, k, L.R, L.ncol, full, empty, stgm_ring, abort_flag);
+    if (threadIdx.x == STG_T) stg_produce<S, MODE, true>(O, k, L.R, L.ncol, full, empty, stgm_ring, abort_flag);
   } else {
     stgm_consume<D, KR, V, S, MODE>(L, O, k, L.R, L.ncol, epoch, full, empty, stgm_ring, abort_flag, G);
   }
